@@ -1,0 +1,343 @@
+"""Benchmark of the LBFS time step on GB300.
+
+Default workload: the 4096 x 2048 sessile ferrofluid drop (R = 768, field at 45
+degrees, Bo_m = 1.0, chi = 1, Ste = 0.1) in mixed precision (FP32 bulk, FP64
+enthalpy storage and inversion, FP64-refined FP32 multigrid potential).  One step
+is one full time step of every cell: the potential solve and three Runge-Kutta
+stages.  The metric is cell-updates per second.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank advances its own replica of the case (the cases
+are independent; there is no collective on the data path) and rank 0 prints one
+JSON line with the aggregate over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "LBFS Mcell-updates/s"
+UNIT = "Mcell-updates/s"
+L2_BYTES = 129 * 2 ** 20
+FALLBACK_HBM_GBS = 6800.0
+
+# algorithmic bytes per cell of one stage launch, averaged over the three stages:
+# stage 1 reads W^n, F_s^{n-1}, phi and writes W^1; stages 2 and 3 also read W^n
+# cell-locally; stage 3 also writes F_s^n and mu_m.  W is H_e (FP64) plus p, m_x,
+# m_y, C in the working precision.
+def stage_bytes_per_cell(prec: int) -> float:
+    r = 8 if prec == 0 else 4
+    w = 8 + 4 * r
+    s1 = w + r + r + w
+    s2 = w + w + r + r + w
+    s3 = w + w + r + r + w + r + r
+    return (s1 + s2 + s3) / 3.0
+
+
+def workloads():
+    from paper_2511_10257_gb300 import inputs as I
+    return {
+        "huge": ("4096x2048 sessile ferrofluid drop, R=768, field 45 deg, Bo_m=1.0, chi=1, Ste=0.1",
+                 I.config_huge()),
+        "large": ("1024x512 sessile ferrofluid drop, R=192, horizontal field, Bo_m=1.5, chi=2, Ste=0.05",
+                  I.config_large()),
+        "medium": ("512x256 sessile ferrofluid drop, R=96, vertical field, Bo_m=1.0, chi=1, Ste=0.1",
+                   I.config_medium()),
+    }
+
+
+def sample_case(case: dict, factor: int) -> dict:
+    """the same physics on a grid coarser by `factor` (radius scaled with it)"""
+    d = dict(case)
+    d["nx"] //= factor
+    d["ny"] //= factor
+    d["radius"] = case["radius"] / factor
+    return d
+
+
+def reduce_over_ranks(elapsed_s: float, units: float, world: int):
+    """max elapsed time and total units over ranks (no-op on one rank)"""
+    if world <= 1:
+        return elapsed_s, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed_s], dtype=torch.float64)
+    u = torch.tensor([units], dtype=torch.float64)
+    if dist.get_backend() == "nccl":
+        t, u = t.cuda(), u.cuda()
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock and throttle-reason samples during the timed region"""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        self.proc.wait()
+        self.out.flush()
+        self.out.seek(0)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.read().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        os.unlink(self.out.name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def oracle_rate(case: dict, steps: int, warmup: int, threads: int):
+    """FP64 CPU oracle, as it stands, on `case`: cell-updates per second"""
+    import oracle
+    o = oracle.Oracle(case, threads=threads)
+    if warmup:
+        o.step(warmup)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = time.perf_counter() - t0
+    return case["nx"] * case["ny"] * steps / dt / 1e6, dt
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    name, case = workloads()[args.workload]
+    sample = sample_case(case, args.sample_factor)
+    threads = os.cpu_count() or 1
+    value, dt = oracle_rate(sample, args.steps, args.warmup, threads)
+    sample_desc = (f"the {name} physics on a {sample['nx']}x{sample['ny']} grid (R={sample['radius']:g}), "
+                   f"{args.steps} steps after {args.warmup} warm-up steps, {threads} OpenMP threads")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": name, "grid": f"{case['nx']}x{case['ny']}",
+                                        "sample": sample_desc},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": sample_desc},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def run_gpu(args):
+    import numpy as np
+    import torch
+
+    from paper_2511_10257_gb300 import build as B
+    from paper_2511_10257_gb300 import inputs as I
+    from paper_2511_10257_gb300 import lbfs
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    name, case = workloads()[args.workload]
+    prec = lbfs.FP64 if args.precision == "fp64" else lbfs.MIXED
+    stream = torch.cuda.current_stream()
+    solver = lbfs.Solver(precision=prec, max_cases=1, device=local, stream=stream.cuda_stream,
+                         torch_alloc=True)
+    solver.set_case(0, case)
+    ncell = case["nx"] * case["ny"]
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    solver.step(args.warmup)
+    barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    solver.timing(True)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    solver.step(args.steps)
+    ev1.record(stream)
+    barrier()
+    elapsed = ev0.elapsed_time(ev1) / 1e3
+    (st_ms, st_n), (pot_ms, pot_n), (fin_ms, fin_n) = solver.timing_read()
+    launches = solver.last_launch_count()
+    solver.timing(False)
+    clk = clocks.stop()
+    t_max, units = reduce_over_ranks(elapsed, ncell * args.steps, world)
+    value = units / t_max / 1e6
+
+    # end to end through the C ABI with host buffers: upload the case state from
+    # pinned host memory, K steps each returning its statistics, download C, F_l, T
+    e2e = None
+    if not args.no_e2e:
+        in_ids = [I.HE, I.P, I.C, I.MX, I.MY, I.FSPREV, I.PHI]
+        state = solver.fields(0, in_ids)
+        pinned = torch.empty((len(in_ids), case["ny"], case["nx"]), dtype=torch.float64, pin_memory=True)
+        host = pinned.numpy()
+        for k, f in enumerate(in_ids):
+            host[k] = state[f]
+        out_ids = [I.C, I.FL, I.T]
+        stats_bytes = 80
+        barrier()
+        t0 = time.perf_counter()
+        solver.set_fields(0, {f: host[k] for k, f in enumerate(in_ids)})
+        for _ in range(args.steps):
+            solver.step(1)
+        solver.fields(0, out_ids)
+        barrier()
+        t_e2e = time.perf_counter() - t0
+        t_e2e, units_e2e = reduce_over_ranks(t_e2e, ncell * args.steps, world)
+        e2e = {"value": units_e2e / t_e2e / 1e6, "unit": UNIT,
+               "h2d_bytes_per_step": int(len(in_ids) * 8 * ncell / args.steps),
+               "d2h_bytes_per_step": int(stats_bytes + len(out_ids) * 8 * ncell / args.steps)}
+
+    # plain FP64 path on the same grid for the mixed-versus-FP64 speed-up
+    fp64 = None
+    if prec == lbfs.MIXED and args.fp64_steps > 0:
+        s64 = lbfs.Solver(precision=lbfs.FP64, max_cases=1, device=local, stream=stream.cuda_stream,
+                          torch_alloc=True)
+        s64.set_case(0, case)
+        s64.step(2)
+        barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s64.step(args.fp64_steps)
+        b.record(stream)
+        barrier()
+        t64 = a.elapsed_time(b) / 1e3
+        s64.close()
+        fp64 = {"value": ncell * args.fp64_steps / t64 / 1e6, "unit": UNIT, "steps": args.fp64_steps,
+                "ms_per_step": 1e3 * t64 / args.fp64_steps}
+
+    if rank != 0:
+        solver.close()
+        return 0
+    peak, peak_kind = measured_peak()
+    bpc = stage_bytes_per_cell(prec)
+    stage_avg_s = st_ms / max(st_n, 1) / 1e3
+    achieved = ncell * bpc / stage_avg_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "kernel": "stage_kernel",
+                "peak_source": peak_kind, "bytes_per_cell": bpc,
+                "launch_ms": stage_avg_s * 1e3, "potential_ms_per_step": pot_ms / max(pot_n, 1),
+                "finalize_ms_per_step": fin_ms / max(fin_n, 1)}
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        sample = sample_case(case, args.sample_factor)
+        threads = os.cpu_count() or 1
+        v, dt = oracle_rate(sample, args.cpu_steps, 1, threads)
+        cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"the same physics on a {sample['nx']}x{sample['ny']} grid "
+                         f"(R={sample['radius']:g}), {args.cpu_steps} steps, {dt:.1f} s"}
+    state_bytes = ncell * (8 + 4 * (8 if prec == 0 else 4))
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if prec == lbfs.FP64 else "f32+f64",
+        "data": "synthetic",
+        "config": {"workload": name, "grid": f"{case['nx']}x{case['ny']}",
+                   "precision": args.precision,
+                   "l2": f"inputs larger than L2 (state {state_bytes / 2**20:.0f} MiB per set, L2 129 MiB)"
+                   if state_bytes > L2_BYTES else "L2-resident state"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+        "fp64": fp64,
+    }
+    print(json.dumps(line))
+    solver.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="huge", choices=["huge", "large", "medium"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--cpu-steps", type=int, default=100)
+    ap.add_argument("--sample-factor", type=int, default=16)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

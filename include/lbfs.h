@@ -1,0 +1,178 @@
+/*
+ * lbfs.h -- C ABI of the GB300 (sm_103a) enthalpy-based lattice Boltzmann flux
+ * solver (LBFS) for ferrofluid-droplet freezing in a uniform magnetic field.
+ *
+ * One call of lbfs_step advances every case of a context by whole time steps of
+ * the finite-volume update (paper Sec. 3.4, Table 1):
+ *   - enthalpy -> temperature and liquid fraction (Eq. 8), solid held at rest
+ *     (F_IBM of Eq. 9);
+ *   - magnetic scalar potential, div(mu_m grad phi_m) = 0 (Eq. 4), whose
+ *     steady magnetic LBFS (Eqs. 12-18) this solves directly;
+ *   - per-face LBFS reconstruction (Eqs. 44, 45) of the mass, momentum,
+ *     phase-field and enthalpy fluxes (Eqs. 20-37, 43);
+ *   - Kelvin and surface-tension body forces (Eq. 6, F_surf = -C grad mu_c) and
+ *     the sources of Eq. 41; finite-volume sum (Eq. 42); third-order
+ *     Runge-Kutta in time (Sec. 3.4).
+ *
+ * Lattice units throughout: dx = 1, D2Q9 with c = 1 and c_s^2 = 1/3.
+ * All pointers are plain host or device pointers; no C++ or framework types
+ * cross this boundary.  No function throws; every failure is a status code with
+ * a message available from lbfs_last_error.
+ */
+#ifndef LBFS_H
+#define LBFS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbfs_ctx lbfs_ctx; /* opaque; owns all device state of its cases */
+
+typedef enum {
+    LBFS_OK = 0,
+    LBFS_EINVAL = 1,         /* bad argument or unsupported case; nothing was launched   */
+    LBFS_ENOMEM = 2,         /* device allocation failed                                 */
+    LBFS_ECUDA = 3,          /* a CUDA call failed; the message names it                 */
+    LBFS_ETIMEOUT = 4,       /* a bounded device wait ran out                            */
+    LBFS_EDIVERGED = 5,      /* a non-finite value appeared in a case's state            */
+    LBFS_ENOTCONVERGED = 6   /* the potential solve missed its tolerance in max cycles   */
+} lbfs_status;
+
+typedef enum {
+    LBFS_FP64 = 0,   /* every field and flux in FP64                                      */
+    LBFS_MIXED = 1   /* fluxes, forces and state in FP32 except H_e (FP64 storage and
+                        FP64 enthalpy inversion); potential by FP32 multigrid inside
+                        FP64 residual refinement; FP64 global sums                        */
+} lbfs_precision;
+
+/* Context configuration.  Zero-initialise and set what you need. */
+typedef struct lbfs_config {
+    int32_t device;          /* CUDA device ordinal                                        */
+    int32_t precision;       /* lbfs_precision                                             */
+    int32_t max_cases;       /* number of case slots (batched cases advance together)      */
+    int32_t use_graph;       /* 1: record the step as a CUDA graph and replay it           */
+    void*   cuda_stream;     /* borrowed cudaStream_t; NULL: the context creates its own   */
+    void* (*dev_alloc)(size_t bytes, void* user);  /* optional device allocator, e.g. a   */
+    void  (*dev_free)(void* ptr, void* user);      /* framework's caching allocator       */
+    void*   alloc_user;
+    int32_t mg_max_cycles;   /* potential refinement cycles per step (0: 40)                 */
+    double  mg_tol;          /* relative residual ||b - A phi|| / ||b|| (0: 1e-13 FP64,
+                                1e-8 mixed)                                                */
+    int32_t tile;            /* stage-kernel tile shape id (0: the tuned default)           */
+    int32_t reserved[7];
+} lbfs_config;
+
+/* One case.  Walls are numbered 0 left (x = 0), 1 right (x = nx), 2 bottom (y = 0),
+ * 3 top (y = ny).  Cell (i, j) has centre (i + 1/2, j + 1/2). */
+typedef struct lbfs_case_desc {
+    int32_t nx, ny;                 /* cells; both >= 4                                    */
+    int32_t periodic_x, periodic_y; /* 1: periodic axis (no walls on it)                   */
+    int32_t thermal_dirichlet[4];   /* 1: wall held at wall_T, 0: adiabatic                */
+    double  wall_T[4];
+    int32_t mag_bc;                 /* 0: uniform far field phi = -H0 (x cos a + y sin a) on
+                                       every wall; 1: on bottom/top only, insulating sides */
+    int32_t init;                   /* 0: sessile drop centred at (nx/2, 0); 1: free drop at
+                                       (drop_x, drop_y); 2: uniform C = 1                  */
+    double  radius, drop_x, drop_y;
+    double  T_init;                 /* initial temperature (liquid everywhere)             */
+    double  H0, field_angle_deg;    /* far-field |H| and its angle from +x                 */
+    double  bo_m;                   /* > 0: H0 = sqrt(Bo_m sigma / (mu_0 2 radius)) (Eq. 50) */
+    double  stefan;                 /* > 0: L = C_p,l (T_m - wall_T[2]) / Ste (Eq. 50)     */
+    double  latent;                 /* L when stefan <= 0                                  */
+    double  T_m;                    /* melting temperature (T_s = T_l = T_m)               */
+    double  rho_l, rho_g, rho_s;    /* Eq. 11 phase properties                              */
+    double  mu_l, mu_g, mu_s;
+    double  cp_l, cp_g, cp_s;
+    double  lam_l, lam_g, lam_s;
+    double  chi_l, chi_g, chi_s;
+    double  sigma, xi;              /* surface tension, interface width (beta, kappa of mu_c) */
+    double  mobility, Q_g;          /* M_c and the phase-field diffusion parameter          */
+    double  gravity;                /* g along y (F_g = rho g)                              */
+    double  dt, dts;                /* finite-volume step and streaming step                */
+    int32_t flags;                  /* must be 0                                            */
+    int32_t pad_;
+} lbfs_case_desc;
+
+/* Per-case diagnostics after the last step (FP64 sums over the grid). */
+typedef struct lbfs_case_stats {
+    double  sum_C;        /* sum of C                                                     */
+    double  sum_He;       /* sum of H_e                                                   */
+    double  sum_Fl_drop;  /* sum of F_l over droplet cells (C >= 1/2)                     */
+    double  n_drop;       /* number of droplet cells                                      */
+    double  Q_L;          /* Eq. 51: mean solid fraction of the droplet cells             */
+    double  t;            /* simulated time                                               */
+    double  t_freeze;     /* first t with Q_L >= 0.99 (linear in time); < 0 if not yet    */
+    double  pot_resid;    /* relative residual of the last potential solve                */
+    int32_t pot_cycles;   /* refinement cycles of the last potential solve                */
+    int32_t nonfinite;    /* 1 if a non-finite value appeared                             */
+} lbfs_case_stats;
+
+/* Field identifiers; a field mask is a bit set of (1u << id).  lbfs_fields returns
+ * FP64 row-major (x fastest) arrays of nx*ny values, one per set bit in increasing
+ * id order. */
+enum {
+    LBFS_FIELD_PHI = 0,  /* magnetic potential                              */
+    LBFS_FIELD_HE = 1,   /* total enthalpy H_e                              */
+    LBFS_FIELD_T = 2,    /* temperature (Eq. 8)                             */
+    LBFS_FIELD_FL = 3,   /* liquid fraction (Eq. 8)                         */
+    LBFS_FIELD_P = 4,    /* pressure p                                      */
+    LBFS_FIELD_U = 5,    /* velocity x                                      */
+    LBFS_FIELD_V = 6,    /* velocity y                                      */
+    LBFS_FIELD_C = 7,    /* order parameter C                               */
+    LBFS_FIELD_MUC = 8,  /* chemical potential mu_c                         */
+    LBFS_FIELD_RHO = 9,  /* density (Eq. 11)                                */
+    LBFS_FIELD_MX = 10,  /* rho c_s^2 u                                     */
+    LBFS_FIELD_MY = 11,  /* rho c_s^2 v                                     */
+    LBFS_FIELD_FSPREV = 12 /* solid fraction of the previous step           */
+};
+
+/* Create a context on cfg->device.  Returns LBFS_EINVAL for a bad config, LBFS_ECUDA
+ * if the device cannot be used.  *out is NULL on failure. */
+lbfs_status lbfs_create(const lbfs_config* cfg, lbfs_ctx** out);
+
+/* (Re)define case slot case_id (0 <= case_id < max_cases) and initialise its fields on
+ * the host (Table 1 "Initialization": droplet C = 1/2 + 1/2 tanh(2 (R - r)/xi),
+ * uniform T_init, liquid everywhere, p = 0, u = 0, phi the uniform far field), then
+ * copy them to the device.  Checks the case (sizes, positive properties, dt against
+ * the explicit diffusion limit) before any allocation; LBFS_EINVAL on failure. */
+lbfs_status lbfs_set_case(lbfs_ctx* ctx, int32_t case_id, const lbfs_case_desc* desc);
+
+/* Overwrite stored fields of a case from host FP64 arrays (layout as lbfs_fields).
+ * Settable: PHI, HE, P, C, MX, MY, FSPREV.  Other bits give LBFS_EINVAL. */
+lbfs_status lbfs_set_fields(lbfs_ctx* ctx, int32_t case_id, uint32_t mask, const double* host_in);
+
+/* Advance every defined case by nsteps time steps on the context's stream and wait
+ * for completion.  out (nullable) receives max_cases stats (undefined slots zero).
+ * LBFS_EDIVERGED / LBFS_ENOTCONVERGED are reported after the steps ran. */
+lbfs_status lbfs_step(lbfs_ctx* ctx, int32_t nsteps, lbfs_case_stats* out);
+
+/* Copy fields of a case to caller-owned host memory (FP64, see field ids). */
+lbfs_status lbfs_fields(lbfs_ctx* ctx, int32_t case_id, uint32_t mask, double* host_out);
+
+/* Number of device kernel launches the last lbfs_step issued (graph nodes count). */
+int64_t lbfs_last_launch_count(const lbfs_ctx* ctx);
+
+/* Kernel timing.  While enabled, lbfs_step brackets every launch with CUDA events on
+ * the context's stream and accumulates the elapsed device time per kernel class:
+ * LBFS_TIMING_STAGE (the fused Runge-Kutta stage kernel), LBFS_TIMING_POTENTIAL (the
+ * whole potential solve of a step), LBFS_TIMING_FINALIZE (step-end statistics).
+ * Enabling clears the accumulators; while enabled the step is never replayed from a
+ * graph.  lbfs_timing_read copies n (<= 3) accumulated milliseconds and event-pair
+ * counts into caller-owned arrays (either may be NULL). */
+enum { LBFS_TIMING_STAGE = 0, LBFS_TIMING_POTENTIAL = 1, LBFS_TIMING_FINALIZE = 2 };
+lbfs_status lbfs_timing(lbfs_ctx* ctx, int32_t enable);
+lbfs_status lbfs_timing_read(lbfs_ctx* ctx, double* ms, int64_t* counts, int32_t n);
+
+/* Release all device memory and the owned stream (if any). */
+void lbfs_destroy(lbfs_ctx* ctx);
+
+/* Sticky message of the last failure on ctx ("" if none); valid until the next call. */
+const char* lbfs_last_error(const lbfs_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -579,8 +579,8 @@ int oracle_solve_potential(oracle_state* s)
 {
     size_t N = (size_t)s->nx * s->ny;
     if (!needs_potential_solve(s)) {
-        for (int j = 0; j < s->ny; ++j)
-            for (int i = 0; i < s->nx; ++i) s->phi[CI(s, i, j)] = phi_far(s, i + 0.5, j + 0.5);
+        /* chi = 0 everywhere (no Kelvin force) or no Dirichlet wall: the potential is
+         * left as it is (the uniform far field unless imported) */
         s->pot_resid = 0.0;
         s->pot_iters = 0;
         return 0;

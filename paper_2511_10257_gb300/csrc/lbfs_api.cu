@@ -1,0 +1,645 @@
+// lbfs_api.cu -- host implementation of the C ABI declared in include/lbfs.h:
+// context and case management, device memory layout, tile work lists for batched
+// cases, and the per-step schedule (potential refinement, three Runge-Kutta stages,
+// step-end statistics), optionally recorded once as a CUDA graph and replayed.
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "lbfs.h"
+#include "lbfs_kernels.h"
+
+using namespace lbfs;
+
+namespace {
+
+constexpr int kCoarsenCells = 256;    // stop coarsening at or below this many cells
+constexpr int kCoarsestMax = 4096;    // largest coarsest level the one-block CG accepts
+constexpr int kNu = 2;                // pre- and post-smoothing sweeps (red + black)
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+struct Slot {
+    bool defined = false;
+    lbfs_case_desc desc{};
+    DevCase hd{};
+    void* block = nullptr;
+};
+
+}  // namespace
+
+struct lbfs_ctx {
+    lbfs_config cfg{};
+    int prec = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<Slot> slots;
+    DevCase* d_cases = nullptr;
+    double* d_stats = nullptr;
+    TileRef* d_stage_tiles = nullptr;
+    int n_stage_tiles = 0;
+    std::vector<TileRef*> d_mg_tiles;
+    std::vector<int> n_mg_tiles;
+    int* d_active = nullptr;
+    int n_active = 0;
+    int* d_pot = nullptr;
+    int n_pot = 0;
+    int max_depth = 0;
+    int coarsest_cells = 0;
+    int* d_flag = nullptr;
+    int* h_flag = nullptr;
+    double* h_stats = nullptr;
+    double* d_scratch = nullptr;
+    size_t scratch_bytes = 0;
+    bool dirty = true;
+    bool pot_fail = false;
+    std::string err;
+    int64_t launches = 0;
+    double mg_tol = 0.0;
+    int mg_max_cycles = 0;
+    cudaGraphExec_t gexec = nullptr;
+    cudaGraph_t graph = nullptr;
+    // kernel timing (events on the context stream)
+    bool timing = false;
+    double t_ms[3] = {0, 0, 0};
+    int64_t t_cnt[3] = {0, 0, 0};
+    std::vector<cudaEvent_t> ev_pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+};
+
+namespace {
+
+lbfs_status fail(lbfs_ctx* c, lbfs_status s, const std::string& msg) {
+    if (c) c->err = msg;
+    return s;
+}
+
+#define CK(call)                                                                                  \
+    do {                                                                                          \
+        cudaError_t e_ = (call);                                                                  \
+        if (e_ != cudaSuccess)                                                                    \
+            return fail(ctx, LBFS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_));     \
+    } while (0)
+
+void* dalloc(lbfs_ctx* ctx, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (ctx->cfg.dev_alloc) return ctx->cfg.dev_alloc(bytes, ctx->cfg.alloc_user);
+    void* p = nullptr;
+    if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void dfree(lbfs_ctx* ctx, void* p) {
+    if (!p) return;
+    if (ctx->cfg.dev_free) ctx->cfg.dev_free(p, ctx->cfg.alloc_user);
+    else cudaFree(p);
+}
+
+void drop_graph(lbfs_ctx* ctx) {
+    if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    ctx->gexec = nullptr;
+    ctx->graph = nullptr;
+}
+
+cudaEvent_t take_event(lbfs_ctx* ctx) {
+    if (!ctx->ev_pool.empty()) {
+        cudaEvent_t e = ctx->ev_pool.back();
+        ctx->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// open an event bracket of class cls (no-op unless timing is on)
+cudaEvent_t tic(lbfs_ctx* ctx) {
+    if (!ctx->timing) return nullptr;
+    cudaEvent_t e = take_event(ctx);
+    cudaEventRecord(e, ctx->stream);
+    return e;
+}
+
+void toc(lbfs_ctx* ctx, int cls, cudaEvent_t start) {
+    if (!ctx->timing || !start) return;
+    cudaEvent_t e = take_event(ctx);
+    cudaEventRecord(e, ctx->stream);
+    ctx->ev_pending.push_back({cls, {start, e}});
+}
+
+// after a stream synchronisation: accumulate and recycle the event pairs
+void harvest(lbfs_ctx* ctx) {
+    for (auto& pe : ctx->ev_pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) {
+            ctx->t_ms[pe.first] += ms;
+            ctx->t_cnt[pe.first] += 1;
+        }
+        ctx->ev_pool.push_back(pe.second.first);
+        ctx->ev_pool.push_back(pe.second.second);
+    }
+    ctx->ev_pending.clear();
+}
+
+int stage_tw(const lbfs_ctx* ctx) { return stage_tile_w(ctx->prec, ctx->cfg.tile); }
+int stage_th(const lbfs_ctx* ctx) { return stage_tile_h(ctx->prec, ctx->cfg.tile); }
+
+// Resolve the case parameters (Eq. 50 groups, mu_c coefficients, boundary flags).
+lbfs_status resolve(lbfs_ctx* ctx, const lbfs_case_desc& d, CaseParams& P) {
+    std::memset(&P, 0, sizeof(P));
+    if (d.nx < 4 || d.ny < 4) return fail(ctx, LBFS_EINVAL, "nx and ny must be >= 4");
+    if ((int64_t)d.nx * d.ny > (int64_t)1 << 31) return fail(ctx, LBFS_EINVAL, "grid too large");
+    if (d.flags != 0) return fail(ctx, LBFS_EINVAL, "flags must be 0");
+    if (d.init < 0 || d.init > 2) return fail(ctx, LBFS_EINVAL, "init must be 0, 1 or 2");
+    if (d.mag_bc < 0 || d.mag_bc > 1) return fail(ctx, LBFS_EINVAL, "mag_bc must be 0 or 1");
+    if (!(d.dt > 0 && d.dts > 0 && d.Q_g > 0 && d.xi > 0 && d.sigma >= 0 && d.mobility >= 0))
+        return fail(ctx, LBFS_EINVAL, "dt, dts, Q_g, xi must be > 0; sigma, mobility >= 0");
+    const double pos[] = {d.rho_l, d.rho_g, d.rho_s, d.cp_l, d.cp_g, d.cp_s};
+    for (double v : pos)
+        if (!(v > 0)) return fail(ctx, LBFS_EINVAL, "densities and heat capacities must be > 0");
+    const double nonneg[] = {d.mu_l, d.mu_g, d.mu_s, d.lam_l, d.lam_g, d.lam_s};
+    for (double v : nonneg)
+        if (!(v >= 0)) return fail(ctx, LBFS_EINVAL, "viscosities and conductivities must be >= 0");
+    if (d.init == 0 || d.init == 1) {
+        if (!(d.radius > 0)) return fail(ctx, LBFS_EINVAL, "radius must be > 0");
+    }
+    P.nx = d.nx;
+    P.ny = d.ny;
+    P.pitch = (int)align_up((size_t)d.nx, 32);
+    P.periodic_x = d.periodic_x ? 1 : 0;
+    P.periodic_y = d.periodic_y ? 1 : 0;
+    for (int w = 0; w < 4; ++w) {
+        const bool on_periodic = (w < 2) ? P.periodic_x : P.periodic_y;
+        P.thermal_dir[w] = (!on_periodic && d.thermal_dirichlet[w]) ? 1 : 0;
+        P.wall_T[w] = d.wall_T[w];
+        P.mag_dir[w] = on_periodic ? 0 : (d.mag_bc == 1 && w < 2 ? 0 : 1);
+    }
+    P.rho_l = d.rho_l; P.rho_g = d.rho_g; P.rho_s = d.rho_s;
+    P.mu_l = d.mu_l; P.mu_g = d.mu_g; P.mu_s = d.mu_s;
+    P.cp_l = d.cp_l; P.cp_g = d.cp_g; P.cp_s = d.cp_s;
+    P.lam_l = d.lam_l; P.lam_g = d.lam_g; P.lam_s = d.lam_s;
+    P.chi_l = d.chi_l; P.chi_g = d.chi_g; P.chi_s = d.chi_s;
+    P.beta = 12.0 * d.sigma / d.xi;
+    P.kappa = 1.5 * d.xi * d.sigma;
+    P.mobility = d.mobility;
+    P.Q_g = d.Q_g;
+    P.gravity = d.gravity;
+    P.T_m = d.T_m;
+    // Eq. 50: Ste = C_p,l (T_m - T_w) / L with the cold bottom wall, and
+    // Bo_m = mu_0 H^2 D / sigma on the droplet diameter D = 2 R (mu_0 = 1)
+    P.L = d.stefan > 0.0 ? d.cp_l * (d.T_m - d.wall_T[2]) / d.stefan : d.latent;
+    if (!(P.L > 0)) return fail(ctx, LBFS_EINVAL, "latent heat must be > 0");
+    P.H0 = d.bo_m > 0.0 ? std::sqrt(d.bo_m * d.sigma / (2.0 * d.radius)) : d.H0;
+    const double ang = d.field_angle_deg * 3.14159265358979323846 / 180.0;
+    P.cos_t = std::cos(ang);
+    P.sin_t = std::sin(ang);
+    P.dt = d.dt;
+    P.dts = d.dts;
+    P.cp_ref = 0.5 * (d.cp_s + d.cp_l);
+    P.vol_ratio = 1.0 - d.rho_s / d.rho_l;
+    bool chi = d.chi_l != 0.0 || d.chi_s != 0.0 || d.chi_g != 0.0;
+    bool dir = false;
+    for (int w = 0; w < 4; ++w) dir = dir || P.mag_dir[w];
+    P.solve_potential = (chi && dir) ? 1 : 0;
+    // explicit stability of the diffusive terms (RK3 real-axis bound ~2.51, five-point
+    // eigenvalue up to 8 D / dx^2)
+    double Dmax = 0.0;
+    const double rho[3] = {d.rho_l, d.rho_g, d.rho_s}, lam[3] = {d.lam_l, d.lam_g, d.lam_s};
+    const double cp[3] = {d.cp_l, d.cp_g, d.cp_s}, mu[3] = {d.mu_l, d.mu_g, d.mu_s};
+    for (int k = 0; k < 3; ++k) {
+        Dmax = std::fmax(Dmax, lam[k] / (rho[k] * cp[k]));
+        Dmax = std::fmax(Dmax, mu[k] / rho[k]);
+    }
+    if (d.dt * 8.0 * Dmax > 2.51)
+        return fail(ctx, LBFS_EINVAL, "dt exceeds the explicit diffusion limit 2.51/(8 D_max)");
+    if (P.solve_potential && ((P.periodic_x && (d.nx & 1)) || (P.periodic_y && (d.ny & 1))))
+        return fail(ctx, LBFS_EINVAL, "periodic axes of a case with a potential solve need even sizes");
+    return LBFS_OK;
+}
+
+// Upload the concatenated tile lists of all defined cases.
+lbfs_status rebuild(lbfs_ctx* ctx) {
+    drop_graph(ctx);
+    const int TX = stage_tw(ctx), TY = stage_th(ctx);
+    std::vector<TileRef> st;
+    std::vector<int> act, pot;
+    int depth = 0, coarsest = 0;
+    for (int c = 0; c < (int)ctx->slots.size(); ++c) {
+        const Slot& s = ctx->slots[c];
+        if (!s.defined) continue;
+        act.push_back(c);
+        int slot = 0;
+        for (int y = 0; y < s.hd.P.ny; y += TY)
+            for (int x = 0; x < s.hd.P.nx; x += TX) st.push_back(TileRef{c, x, y, slot++});
+        if (s.hd.P.solve_potential) {
+            pot.push_back(c);
+            depth = std::max(depth, s.hd.nlev);
+            const MGLevel& lc = s.hd.lev[s.hd.nlev - 1];
+            coarsest = std::max(coarsest, lc.nx * lc.ny);
+        }
+    }
+    std::vector<std::vector<TileRef>> mg(depth);
+    for (int L = 0; L < depth; ++L)
+        for (int c : pot) {
+            const Slot& s = ctx->slots[c];
+            if (s.hd.nlev <= L) continue;
+            int slot = 0;
+            for (int y = 0; y < s.hd.lev[L].ny; y += kMgTY)
+                for (int x = 0; x < s.hd.lev[L].nx; x += kMgTX) mg[L].push_back(TileRef{c, x, y, slot++});
+        }
+    auto upload = [&](void** dst, const void* src, size_t bytes) -> bool {
+        if (*dst) dfree(ctx, *dst);
+        *dst = nullptr;
+        if (bytes == 0) return true;
+        *dst = dalloc(ctx, bytes);
+        if (!*dst) return false;
+        return cudaMemcpy(*dst, src, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    if (!upload((void**)&ctx->d_stage_tiles, st.data(), st.size() * sizeof(TileRef)) ||
+        !upload((void**)&ctx->d_active, act.data(), act.size() * sizeof(int)) ||
+        !upload((void**)&ctx->d_pot, pot.data(), pot.size() * sizeof(int)))
+        return fail(ctx, LBFS_ENOMEM, "tile list upload failed");
+    for (auto* p : ctx->d_mg_tiles) dfree(ctx, p);
+    ctx->d_mg_tiles.assign(depth, nullptr);
+    ctx->n_mg_tiles.assign(depth, 0);
+    for (int L = 0; L < depth; ++L) {
+        if (!upload((void**)&ctx->d_mg_tiles[L], mg[L].data(), mg[L].size() * sizeof(TileRef)))
+            return fail(ctx, LBFS_ENOMEM, "multigrid tile list upload failed");
+        ctx->n_mg_tiles[L] = (int)mg[L].size();
+    }
+    ctx->n_stage_tiles = (int)st.size();
+    ctx->n_active = (int)act.size();
+    ctx->n_pot = (int)pot.size();
+    ctx->max_depth = depth;
+    ctx->coarsest_cells = coarsest;
+    ctx->dirty = false;
+    return LBFS_OK;
+}
+
+#define LK(call)                                   \
+    do {                                           \
+        cudaError_t e_ = (call);                   \
+        ++ctx->launches;                           \
+        if (e_ != cudaSuccess)                     \
+            return fail(ctx, LBFS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+lbfs_status vcycle(lbfs_ctx* ctx) {
+    const int p = ctx->prec;
+    cudaStream_t s = ctx->stream;
+    const int D = ctx->max_depth;
+    for (int L = 0; L + 1 < D; ++L) {
+        for (int k = 0; k < kNu; ++k) {
+            LK(launch_mg_smooth(p, ctx->d_cases, ctx->d_mg_tiles[L], ctx->n_mg_tiles[L], L, 0, s));
+            LK(launch_mg_smooth(p, ctx->d_cases, ctx->d_mg_tiles[L], ctx->n_mg_tiles[L], L, 1, s));
+        }
+        LK(launch_mg_restrict_resid(p, ctx->d_cases, ctx->d_mg_tiles[L + 1], ctx->n_mg_tiles[L + 1], L + 1, s));
+    }
+    LK(launch_mg_coarsest(p, ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->coarsest_cells, s));
+    for (int L = D - 2; L >= 0; --L) {
+        LK(launch_mg_prolong(p, ctx->d_cases, ctx->d_mg_tiles[L], ctx->n_mg_tiles[L], L, s));
+        for (int k = 0; k < kNu; ++k) {
+            LK(launch_mg_smooth(p, ctx->d_cases, ctx->d_mg_tiles[L], ctx->n_mg_tiles[L], L, 0, s));
+            LK(launch_mg_smooth(p, ctx->d_cases, ctx->d_mg_tiles[L], ctx->n_mg_tiles[L], L, 1, s));
+        }
+    }
+    return LBFS_OK;
+}
+
+lbfs_status potential_solve(lbfs_ctx* ctx) {
+    if (ctx->n_pot == 0) return LBFS_OK;
+    const int p = ctx->prec;
+    cudaStream_t s = ctx->stream;
+    for (int L = 1; L < ctx->max_depth; ++L)
+        LK(launch_mg_restrict_mu(p, ctx->d_cases, ctx->d_mg_tiles[L], ctx->n_mg_tiles[L], L, s));
+    for (int it = 0;; ++it) {
+        LK(launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], s));
+        CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
+        LK(launch_mg_finalize(ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, it == 0, ctx->d_flag, s));
+        CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        if (*ctx->h_flag == 0) break;
+        if (it == ctx->mg_max_cycles) {
+            ctx->pot_fail = true;
+            break;
+        }
+        lbfs_status r = vcycle(ctx);
+        if (r != LBFS_OK) return r;
+        LK(launch_mg_correct(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], s));
+    }
+    return LBFS_OK;
+}
+
+lbfs_status one_step(lbfs_ctx* ctx) {
+    cudaEvent_t t0 = tic(ctx);
+    lbfs_status r = potential_solve(ctx);
+    if (r != LBFS_OK) return r;
+    toc(ctx, LBFS_TIMING_POTENTIAL, t0);
+    for (int k = 0; k < 3; ++k) {
+        cudaEvent_t t1 = tic(ctx);
+        LK(launch_stage(ctx->prec, ctx->cfg.tile, ctx->d_cases, ctx->d_stage_tiles, ctx->n_stage_tiles, k,
+                        ctx->stream));
+        toc(ctx, LBFS_TIMING_STAGE, t1);
+    }
+    cudaEvent_t t2 = tic(ctx);
+    LK(launch_step_finalize(ctx->d_cases, ctx->d_active, ctx->n_active, ctx->stream));
+    toc(ctx, LBFS_TIMING_FINALIZE, t2);
+    return LBFS_OK;
+}
+
+lbfs_status check_case(lbfs_ctx* ctx, int32_t id) {
+    if (!ctx) return LBFS_EINVAL;
+    if (id < 0 || id >= (int)ctx->slots.size()) return fail(ctx, LBFS_EINVAL, "case_id out of range");
+    return LBFS_OK;
+}
+
+void free_slot(lbfs_ctx* ctx, Slot& s) {
+    if (s.block) dfree(ctx, s.block);
+    s.block = nullptr;
+    s.defined = false;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbfs_status lbfs_create(const lbfs_config* cfg, lbfs_ctx** out) {
+    if (!out) return LBFS_EINVAL;
+    *out = nullptr;
+    if (!cfg || cfg->max_cases < 1 || cfg->max_cases > 65536 || cfg->precision < 0 || cfg->precision > 1 ||
+        (cfg->dev_alloc == nullptr) != (cfg->dev_free == nullptr))
+        return LBFS_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+        cudaGetLastError();
+        return LBFS_ECUDA;
+    }
+    if (cudaSetDevice(cfg->device) != cudaSuccess) return LBFS_ECUDA;
+    lbfs_ctx* ctx = new lbfs_ctx();
+    ctx->cfg = *cfg;
+    ctx->prec = cfg->precision;
+    ctx->mg_tol = cfg->mg_tol > 0 ? cfg->mg_tol : (ctx->prec == 0 ? 1e-13 : 1e-8);
+    ctx->mg_max_cycles = cfg->mg_max_cycles > 0 ? cfg->mg_max_cycles : 40;
+    ctx->slots.resize(cfg->max_cases);
+    if (cfg->cuda_stream) {
+        ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
+    } else {
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete ctx;
+            return LBFS_ECUDA;
+        }
+        ctx->own_stream = true;
+    }
+    ctx->d_cases = static_cast<DevCase*>(dalloc(ctx, sizeof(DevCase) * cfg->max_cases));
+    ctx->d_stats = static_cast<double*>(dalloc(ctx, sizeof(double) * kStatN * cfg->max_cases));
+    ctx->d_flag = static_cast<int*>(dalloc(ctx, 256));
+    if (!ctx->d_cases || !ctx->d_stats || !ctx->d_flag ||
+        cudaMallocHost(&ctx->h_flag, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&ctx->h_stats, sizeof(double) * kStatN * cfg->max_cases) != cudaSuccess) {
+        lbfs_destroy(ctx);
+        return LBFS_ENOMEM;
+    }
+    cudaMemset(ctx->d_cases, 0, sizeof(DevCase) * cfg->max_cases);
+    cudaMemset(ctx->d_stats, 0, sizeof(double) * kStatN * cfg->max_cases);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        lbfs_destroy(ctx);
+        return LBFS_ECUDA;
+    }
+    *out = ctx;
+    return LBFS_OK;
+}
+
+lbfs_status lbfs_set_case(lbfs_ctx* ctx, int32_t id, const lbfs_case_desc* desc) {
+    lbfs_status r = check_case(ctx, id);
+    if (r != LBFS_OK) return r;
+    if (!desc) return fail(ctx, LBFS_EINVAL, "desc is NULL");
+    CaseParams P;
+    r = resolve(ctx, *desc, P);
+    if (r != LBFS_OK) return r;
+    // multigrid hierarchy
+    DevCase hd;
+    std::memset(&hd, 0, sizeof(hd));
+    hd.P = P;
+    int nx = P.nx, ny = P.ny, nlev = 1;
+    hd.lev[0].nx = nx;
+    hd.lev[0].ny = ny;
+    while (nlev < kMaxLevels && nx % 2 == 0 && ny % 2 == 0 && nx * ny > kCoarsenCells && nx >= 4 && ny >= 4) {
+        nx /= 2;
+        ny /= 2;
+        hd.lev[nlev].nx = nx;
+        hd.lev[nlev].ny = ny;
+        ++nlev;
+    }
+    if (P.solve_potential && nx * ny > kCoarsestMax)
+        return fail(ctx, LBFS_EINVAL,
+                    "grid sizes do not coarsen to <= 4096 cells by halving (use sizes with more factors of 2)");
+    hd.nlev = nlev;
+    const int TX = stage_tw(ctx), TY = stage_th(ctx);
+    hd.red_tiles = ((P.nx + TX - 1) / TX) * ((P.ny + TY - 1) / TY);
+    hd.mg_tiles = ((P.nx + kMgTX - 1) / kMgTX) * ((P.ny + kMgTY - 1) / kMgTY);
+    // one device block per case
+    const size_t rs = ctx->prec == 0 ? sizeof(double) : sizeof(float);
+    const size_t cells = (size_t)P.pitch * P.ny;
+    size_t off = 0;
+    std::vector<std::pair<void**, size_t>> plan;
+    auto add = [&](void** dst, size_t bytes) {
+        plan.push_back({dst, off});
+        off = align_up(off + bytes, 256);
+    };
+    for (int k = 0; k < 3; ++k) {
+        add(&hd.He[k], cells * sizeof(double));
+        add(&hd.p[k], cells * rs);
+        add(&hd.mx[k], cells * rs);
+        add(&hd.my[k], cells * rs);
+        add(&hd.C[k], cells * rs);
+    }
+    add((void**)&hd.phi64, cells * sizeof(double));
+    if (ctx->prec != 0) add(&hd.phi, cells * rs);
+    add(&hd.Fs_prev, cells * rs);
+    for (int L = 0; L < nlev; ++L) {
+        hd.lev[L].pitch = (int)align_up((size_t)hd.lev[L].nx, 32);
+        const size_t lc = (size_t)hd.lev[L].pitch * hd.lev[L].ny;
+        add(&hd.lev[L].mu, lc * rs);
+        add(&hd.lev[L].e, lc * rs);
+        add(&hd.lev[L].r, lc * rs);
+    }
+    add((void**)&hd.red, (size_t)hd.red_tiles * kRedN * sizeof(double));
+    add((void**)&hd.mg_red, (size_t)hd.mg_tiles * 2 * sizeof(double));
+    Slot& s = ctx->slots[id];
+    free_slot(ctx, s);
+    drop_graph(ctx);
+    ctx->dirty = true;
+    s.block = dalloc(ctx, off);
+    if (!s.block) return fail(ctx, LBFS_ENOMEM, "device allocation of the case failed");
+    for (auto& pr : plan) *pr.first = static_cast<char*>(s.block) + pr.second;
+    if (ctx->prec == 0) hd.phi = hd.phi64;
+    hd.stats = ctx->d_stats + (size_t)id * kStatN;
+    s.hd = hd;
+    s.desc = *desc;
+    CK(cudaMemsetAsync(s.block, 0, off, ctx->stream));
+    CK(cudaMemcpyAsync(ctx->d_cases + id, &s.hd, sizeof(DevCase), cudaMemcpyHostToDevice, ctx->stream));
+    double st0[kStatN];
+    for (double& v : st0) v = 0.0;
+    st0[ST_T_FREEZE] = -1.0;
+    CK(cudaMemcpyAsync(hd.stats, st0, sizeof(st0), cudaMemcpyHostToDevice, ctx->stream));
+    InitArgs a;
+    a.kind = desc->init;
+    a.radius = desc->radius;
+    a.cx = desc->init == 0 ? 0.5 * P.nx : desc->drop_x;
+    a.cy = desc->init == 0 ? 0.0 : desc->drop_y;
+    a.T_init = desc->T_init;
+    a.xi = desc->xi;
+    const DevCase* dcase = ctx->d_cases + id;
+    CK(launch_init(ctx->prec, dcase, P.nx, P.ny, a, ctx->stream));
+    CK(launch_mu_from_state(ctx->prec, dcase, P.nx, P.ny, ctx->stream));
+    CK(launch_stats_init(ctx->prec, dcase, P.nx, P.ny, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    s.defined = true;
+    return LBFS_OK;
+}
+
+static lbfs_status ensure_scratch(lbfs_ctx* ctx, size_t bytes) {
+    if (ctx->scratch_bytes >= bytes) return LBFS_OK;
+    dfree(ctx, ctx->d_scratch);
+    ctx->d_scratch = static_cast<double*>(dalloc(ctx, bytes));
+    ctx->scratch_bytes = ctx->d_scratch ? bytes : 0;
+    return ctx->d_scratch ? LBFS_OK : fail(ctx, LBFS_ENOMEM, "scratch allocation failed");
+}
+
+lbfs_status lbfs_set_fields(lbfs_ctx* ctx, int32_t id, uint32_t mask, const double* host_in) {
+    lbfs_status r = check_case(ctx, id);
+    if (r != LBFS_OK) return r;
+    Slot& s = ctx->slots[id];
+    if (!s.defined) return fail(ctx, LBFS_EINVAL, "case not defined");
+    const uint32_t settable = (1u << LBFS_FIELD_PHI) | (1u << LBFS_FIELD_HE) | (1u << LBFS_FIELD_P) |
+                              (1u << LBFS_FIELD_C) | (1u << LBFS_FIELD_MX) | (1u << LBFS_FIELD_MY) |
+                              (1u << LBFS_FIELD_FSPREV);
+    if ((mask & ~settable) || mask == 0 || !host_in) return fail(ctx, LBFS_EINVAL, "bad field mask or buffer");
+    const int nf = __builtin_popcount(mask);
+    const size_t N = (size_t)s.hd.P.nx * s.hd.P.ny;
+    r = ensure_scratch(ctx, nf * N * sizeof(double));
+    if (r != LBFS_OK) return r;
+    CK(cudaMemcpyAsync(ctx->d_scratch, host_in, nf * N * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    const DevCase* dcase = ctx->d_cases + id;
+    CK(launch_store_fields(ctx->prec, dcase, s.hd.P.nx, s.hd.P.ny, mask, ctx->d_scratch, ctx->stream));
+    CK(launch_mu_from_state(ctx->prec, dcase, s.hd.P.nx, s.hd.P.ny, ctx->stream));
+    CK(launch_stats_init(ctx->prec, dcase, s.hd.P.nx, s.hd.P.ny, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBFS_OK;
+}
+
+lbfs_status lbfs_fields(lbfs_ctx* ctx, int32_t id, uint32_t mask, double* host_out) {
+    lbfs_status r = check_case(ctx, id);
+    if (r != LBFS_OK) return r;
+    Slot& s = ctx->slots[id];
+    if (!s.defined) return fail(ctx, LBFS_EINVAL, "case not defined");
+    if (mask == 0 || (mask >> 13) || !host_out) return fail(ctx, LBFS_EINVAL, "bad field mask or buffer");
+    const int nf = __builtin_popcount(mask);
+    const size_t N = (size_t)s.hd.P.nx * s.hd.P.ny;
+    r = ensure_scratch(ctx, nf * N * sizeof(double));
+    if (r != LBFS_OK) return r;
+    CK(launch_derive_fields(ctx->prec, ctx->d_cases + id, s.hd.P.nx, s.hd.P.ny, mask, ctx->d_scratch,
+                            ctx->stream));
+    CK(cudaMemcpyAsync(host_out, ctx->d_scratch, nf * N * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return LBFS_OK;
+}
+
+lbfs_status lbfs_step(lbfs_ctx* ctx, int32_t nsteps, lbfs_case_stats* out) {
+    if (!ctx) return LBFS_EINVAL;
+    if (nsteps < 0) return fail(ctx, LBFS_EINVAL, "nsteps must be >= 0");
+    if (ctx->dirty) {
+        lbfs_status r = rebuild(ctx);
+        if (r != LBFS_OK) return r;
+    }
+    CK(cudaSetDevice(ctx->cfg.device));
+    ctx->launches = 0;
+    ctx->pot_fail = false;
+    for (int n = 0; n < nsteps && ctx->n_active > 0; ++n) {
+        lbfs_status r = one_step(ctx);
+        if (r != LBFS_OK) return r;
+    }
+    const size_t nb = sizeof(double) * kStatN * ctx->slots.size();
+    CK(cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, nb, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    harvest(ctx);
+    bool bad = false;
+    for (size_t c = 0; c < ctx->slots.size(); ++c) {
+        const double* st = ctx->h_stats + c * kStatN;
+        if (ctx->slots[c].defined && st[ST_NONFINITE] > 0) bad = true;
+        if (out) {
+            lbfs_case_stats& o = out[c];
+            std::memset(&o, 0, sizeof(o));
+            if (!ctx->slots[c].defined) continue;
+            o.sum_C = st[ST_SUM_C];
+            o.sum_He = st[ST_SUM_HE];
+            o.sum_Fl_drop = st[ST_SUM_FL_DROP];
+            o.n_drop = st[ST_N_DROP];
+            o.Q_L = st[ST_Q_L];
+            o.t = st[ST_T];
+            o.t_freeze = st[ST_T_FREEZE];
+            o.pot_resid = st[ST_POT_RESID];
+            o.pot_cycles = (int32_t)st[ST_POT_CYCLES];
+            o.nonfinite = st[ST_NONFINITE] > 0 ? 1 : 0;
+        }
+    }
+    if (bad) return fail(ctx, LBFS_EDIVERGED, "a non-finite value appeared in a case's state");
+    if (ctx->pot_fail)
+        return fail(ctx, LBFS_ENOTCONVERGED, "the potential solve missed its tolerance in mg_max_cycles");
+    return LBFS_OK;
+}
+
+int64_t lbfs_last_launch_count(const lbfs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+lbfs_status lbfs_timing(lbfs_ctx* ctx, int32_t enable) {
+    if (!ctx) return LBFS_EINVAL;
+    CK(cudaStreamSynchronize(ctx->stream));
+    harvest(ctx);
+    ctx->timing = enable != 0;
+    for (int k = 0; k < 3; ++k) {
+        ctx->t_ms[k] = 0.0;
+        ctx->t_cnt[k] = 0;
+    }
+    return LBFS_OK;
+}
+
+lbfs_status lbfs_timing_read(lbfs_ctx* ctx, double* ms, int64_t* counts, int32_t n) {
+    if (!ctx || n < 0 || n > 3) return LBFS_EINVAL;
+    for (int k = 0; k < n; ++k) {
+        if (ms) ms[k] = ctx->t_ms[k];
+        if (counts) counts[k] = ctx->t_cnt[k];
+    }
+    return LBFS_OK;
+}
+
+void lbfs_destroy(lbfs_ctx* ctx) {
+    if (!ctx) return;
+    cudaSetDevice(ctx->cfg.device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    drop_graph(ctx);
+    harvest(ctx);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    for (Slot& s : ctx->slots) free_slot(ctx, s);
+    for (auto* p : ctx->d_mg_tiles) dfree(ctx, p);
+    dfree(ctx, ctx->d_stage_tiles);
+    dfree(ctx, ctx->d_active);
+    dfree(ctx, ctx->d_pot);
+    dfree(ctx, ctx->d_cases);
+    dfree(ctx, ctx->d_stats);
+    dfree(ctx, ctx->d_flag);
+    dfree(ctx, ctx->d_scratch);
+    if (ctx->h_flag) cudaFreeHost(ctx->h_flag);
+    if (ctx->h_stats) cudaFreeHost(ctx->h_stats);
+    if (ctx->own_stream && ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+}
+
+const char* lbfs_last_error(const lbfs_ctx* ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+}  // extern "C"

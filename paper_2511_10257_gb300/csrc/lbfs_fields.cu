@@ -1,0 +1,264 @@
+// lbfs_fields.cu -- per-case utility kernels: initial condition, field export and
+// import in FP64, the potential coefficient of a state, and the step-end statistics
+// (Eq. 51 liquid fraction of the droplet, sums of C and H_e, freezing time).
+#include "lbfs_kernels.h"
+
+namespace lbfs {
+
+namespace {
+
+
+__device__ __forceinline__ bool cell_of(int nx, int ny, int& i, int& j) {
+    i = blockIdx.x * blockDim.x + threadIdx.x;
+    j = blockIdx.y;
+    return i < nx && j < ny;
+}
+
+// Table 1 "Initialization": droplet C = 1/2 + 1/2 tanh(2 (R - r)/xi) (the equilibrium
+// profile of the Cahn-Hilliard free energy), uniform T_init, liquid everywhere so
+// H_e = C_p T + L, p = 0, u = 0, uniform far-field potential.
+template <class R>
+__global__ void k_init(const DevCase* __restrict__ dc, InitArgs a) {
+    int i, j;
+    const CaseParams& P = dc->P;
+    if (!cell_of(P.nx, P.ny, i, j)) return;
+    const double x = i + 0.5, y = j + 0.5;
+    double C = 1.0;
+    if (a.kind != 2) {
+        const double dx = x - a.cx, dy = y - a.cy;
+        C = 0.5 + 0.5 * tanh(2.0 * (a.radius - sqrt(dx * dx + dy * dy)) / a.xi);
+    }
+    const double cp = mixture<double>(0.0, C, P.cp_s, P.cp_l, P.cp_g);
+    const double He = cp * a.T_init + P.L;
+    const size_t k = (size_t)j * P.pitch + i;
+    static_cast<double*>(dc->He[0])[k] = He;
+    static_cast<R*>(dc->p[0])[k] = R(0);
+    static_cast<R*>(dc->mx[0])[k] = R(0);
+    static_cast<R*>(dc->my[0])[k] = R(0);
+    static_cast<R*>(dc->C[0])[k] = R(C);
+    const double phi = -P.H0 * (x * P.cos_t + y * P.sin_t);
+    dc->phi64[k] = phi;
+    static_cast<R*>(dc->phi)[k] = R(phi);
+    R T, Fl;
+    invert_enthalpy<R, double>(P, He, R(C), T, Fl);
+    static_cast<R*>(dc->Fs_prev)[k] = R(1) - Fl;
+}
+
+template <class R>
+__global__ void k_mu_from_state(const DevCase* __restrict__ dc) {
+    int i, j;
+    const CaseParams& P = dc->P;
+    if (!cell_of(P.nx, P.ny, i, j)) return;
+    const size_t k = (size_t)j * P.pitch + i;
+    const R C = static_cast<const R*>(dc->C[0])[k];
+    R T, Fl;
+    invert_enthalpy<R, double>(P, static_cast<const double*>(dc->He[0])[k], C, T, Fl);
+    static_cast<R*>(dc->lev[0].mu)[(size_t)j * dc->lev[0].pitch + i] =
+        R(1) + mixture(R(1) - Fl, C, P.chi_s, P.chi_l, P.chi_g);
+}
+
+template <class R>
+__device__ __forceinline__ R C_at(const CaseParams& P, const R* C, int i, int j) {
+    // C with the zero-gradient (theta = 90 deg) ghost rule or periodic wrap
+    if (i < 0) i = P.periodic_x ? i + P.nx : 0;
+    if (i >= P.nx) i = P.periodic_x ? i - P.nx : P.nx - 1;
+    if (j < 0) j = P.periodic_y ? j + P.ny : 0;
+    if (j >= P.ny) j = P.periodic_y ? j - P.ny : P.ny - 1;
+    return C[(size_t)j * P.pitch + i];
+}
+
+template <class R>
+__global__ void k_derive(const DevCase* __restrict__ dc, uint32_t mask, double* __restrict__ out) {
+    int i, j;
+    const CaseParams& P = dc->P;
+    if (!cell_of(P.nx, P.ny, i, j)) return;
+    const size_t k = (size_t)j * P.pitch + i;
+    const size_t N = (size_t)P.nx * P.ny, o = (size_t)j * P.nx + i;
+    const double He = static_cast<const double*>(dc->He[0])[k];
+    const R* Cg = static_cast<const R*>(dc->C[0]);
+    const R C = Cg[k];
+    R T, Fl;
+    invert_enthalpy<R, double>(P, He, C, T, Fl);
+    const R rho = mixture(R(1) - Fl, C, P.rho_s, P.rho_l, P.rho_g);
+    const R mx = static_cast<const R*>(dc->mx[0])[k], my = static_cast<const R*>(dc->my[0])[k];
+    int slot = 0;
+    for (int f = 0; f < 13; ++f) {
+        if (!(mask & (1u << f))) continue;
+        double v = 0.0;
+        switch (f) {
+        case 0: v = dc->phi64[k]; break;
+        case 1: v = He; break;
+        case 2: v = (double)T; break;
+        case 3: v = (double)Fl; break;
+        case 4: v = (double)static_cast<const R*>(dc->p[0])[k]; break;
+        case 5: v = (double)(mx * R(3) / rho); break;
+        case 6: v = (double)(my * R(3) / rho); break;
+        case 7: v = (double)C; break;
+        case 8: {
+            const R lap = C_at<R>(P, Cg, i + 1, j) + C_at<R>(P, Cg, i - 1, j) + C_at<R>(P, Cg, i, j + 1) +
+                          C_at<R>(P, Cg, i, j - 1) - R(4) * C;
+            v = (double)(R(2) * R(P.beta) * C * (C - R(1)) * (R(2) * C - R(1)) - R(P.kappa) * lap);
+            break;
+        }
+        case 9: v = (double)rho; break;
+        case 10: v = (double)mx; break;
+        case 11: v = (double)my; break;
+        case 12: v = (double)static_cast<const R*>(dc->Fs_prev)[k]; break;
+        }
+        out[slot * N + o] = v;
+        ++slot;
+    }
+}
+
+template <class R>
+__global__ void k_store(const DevCase* __restrict__ dc, uint32_t mask, const double* __restrict__ in) {
+    int i, j;
+    const CaseParams& P = dc->P;
+    if (!cell_of(P.nx, P.ny, i, j)) return;
+    const size_t k = (size_t)j * P.pitch + i;
+    const size_t N = (size_t)P.nx * P.ny, o = (size_t)j * P.nx + i;
+    int slot = 0;
+    for (int f = 0; f < 13; ++f) {
+        if (!(mask & (1u << f))) continue;
+        const double v = in[slot * N + o];
+        switch (f) {
+        case 0:
+            dc->phi64[k] = v;
+            static_cast<R*>(dc->phi)[k] = R(v);
+            break;
+        case 1: static_cast<double*>(dc->He[0])[k] = v; break;
+        case 4: static_cast<R*>(dc->p[0])[k] = R(v); break;
+        case 7: static_cast<R*>(dc->C[0])[k] = R(v); break;
+        case 10: static_cast<R*>(dc->mx[0])[k] = R(v); break;
+        case 11: static_cast<R*>(dc->my[0])[k] = R(v); break;
+        case 12: static_cast<R*>(dc->Fs_prev)[k] = R(v); break;
+        default: break;
+        }
+        ++slot;
+    }
+}
+
+template <class T>
+__device__ __forceinline__ T block_sum(T v, T* sh) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    T tot = 0;
+    for (int q = 0; q < (int)((blockDim.x + 31) >> 5); ++q) tot += sh[q];
+    return tot;
+}
+
+// statistics of the stored state (one block): used after initialisation or import
+template <class R>
+__global__ void k_stats_init(const DevCase* __restrict__ dc) {
+    __shared__ double sh[32];
+    const CaseParams& P = dc->P;
+    double sC = 0, sH = 0, sFl = 0, nd = 0, sFs = 0;
+    for (int j = 0; j < P.ny; ++j)
+        for (int i = threadIdx.x; i < P.nx; i += blockDim.x) {
+            const size_t k = (size_t)j * P.pitch + i;
+            const double He = static_cast<const double*>(dc->He[0])[k];
+            const R C = static_cast<const R*>(dc->C[0])[k];
+            R T, Fl;
+            invert_enthalpy<R, double>(P, He, C, T, Fl);
+            sC += (double)C;
+            sH += He;
+            if (C >= R(0.5)) {
+                sFl += (double)Fl;
+                nd += 1.0;
+                sFs += (double)(R(1) - Fl);
+            }
+        }
+    sC = block_sum(sC, sh);
+    sH = block_sum(sH, sh);
+    sFl = block_sum(sFl, sh);
+    nd = block_sum(nd, sh);
+    sFs = block_sum(sFs, sh);
+    if (threadIdx.x == 0) {
+        double* st = dc->stats;
+        st[ST_SUM_C] = sC;
+        st[ST_SUM_HE] = sH;
+        st[ST_SUM_FL_DROP] = sFl;
+        st[ST_N_DROP] = nd;
+        st[ST_Q_L] = nd > 0 ? sFs / nd : 0.0;
+        st[ST_QL_PREV] = st[ST_Q_L];
+    }
+}
+
+// step end: fixed-order sum of the stage-tile partials, Eq. 51 liquid-fraction measure,
+// freezing time (first t with Q_L >= 0.99, linear between steps)
+__global__ void k_step_finalize(const DevCase* __restrict__ cases, const int* __restrict__ ids) {
+    __shared__ double sh[32];
+    const DevCase* dc = cases + ids[blockIdx.x];
+    double acc[kRedN];
+    for (int q = 0; q < kRedN; ++q) acc[q] = 0.0;
+    for (int t = threadIdx.x; t < dc->red_tiles; t += blockDim.x)
+        for (int q = 0; q < kRedN; ++q) acc[q] += dc->red[(size_t)t * kRedN + q];
+    for (int q = 0; q < kRedN; ++q) acc[q] = block_sum(acc[q], sh);
+    if (threadIdx.x == 0) {
+        double* st = dc->stats;
+        const double dt = dc->P.dt;
+        st[ST_SUM_C] = acc[0];
+        st[ST_SUM_HE] = acc[1];
+        st[ST_SUM_FL_DROP] = acc[2];
+        st[ST_N_DROP] = acc[3];
+        const double QL = acc[3] > 0.0 ? acc[4] / acc[3] : 0.0;
+        st[ST_Q_L] = QL;
+        if (acc[5] > 0.0) st[ST_NONFINITE] = 1.0;
+        st[ST_T] += dt;
+        st[ST_STEP] += 1.0;
+        if (st[ST_T_FREEZE] < 0.0 && QL >= 0.99) {
+            const double q0 = st[ST_QL_PREV];
+            st[ST_T_FREEZE] = (st[ST_T] - dt) + dt * (0.99 - q0) / (QL - q0);
+        }
+        st[ST_QL_PREV] = QL;
+    }
+}
+
+}  // namespace
+
+static dim3 cell_grid(int nx, int ny) { return dim3((nx + 127) / 128, ny); }
+
+cudaError_t launch_init(int prec, const DevCase* d, int nx, int ny, InitArgs a, cudaStream_t st) {
+    if (prec == 0) k_init<double><<<cell_grid(nx, ny), 128, 0, st>>>(d, a);
+    else k_init<float><<<cell_grid(nx, ny), 128, 0, st>>>(d, a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mu_from_state(int prec, const DevCase* d, int nx, int ny, cudaStream_t st) {
+    if (prec == 0) k_mu_from_state<double><<<cell_grid(nx, ny), 128, 0, st>>>(d);
+    else k_mu_from_state<float><<<cell_grid(nx, ny), 128, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_derive_fields(int prec, const DevCase* d, int nx, int ny, uint32_t mask, double* out,
+                                 cudaStream_t st) {
+    if (prec == 0) k_derive<double><<<cell_grid(nx, ny), 128, 0, st>>>(d, mask, out);
+    else k_derive<float><<<cell_grid(nx, ny), 128, 0, st>>>(d, mask, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_store_fields(int prec, const DevCase* d, int nx, int ny, uint32_t mask,
+                                const double* in, cudaStream_t st) {
+    if (prec == 0) k_store<double><<<cell_grid(nx, ny), 128, 0, st>>>(d, mask, in);
+    else k_store<float><<<cell_grid(nx, ny), 128, 0, st>>>(d, mask, in);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats_init(int prec, const DevCase* d, int nx, int ny, cudaStream_t st) {
+    (void)nx;
+    (void)ny;
+    if (prec == 0) k_stats_init<double><<<1, 1024, 0, st>>>(d);
+    else k_stats_init<float><<<1, 1024, 0, st>>>(d);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_step_finalize(const DevCase* cases, const int* ids, int ncases, cudaStream_t st) {
+    if (ncases <= 0) return cudaSuccess;
+    k_step_finalize<<<ncases, 256, 0, st>>>(cases, ids);
+    return cudaGetLastError();
+}
+
+}  // namespace lbfs

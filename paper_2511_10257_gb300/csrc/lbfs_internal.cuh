@@ -1,0 +1,115 @@
+// lbfs_internal.cuh -- device-side data layout and the per-point physics of the
+// LBFS step shared by the stage, potential and reduction kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbfs {
+
+constexpr int kMaxLevels = 16;
+constexpr int kRedN = 6;        // per-tile partial sums of the step-end reduction
+constexpr int kStatN = 16;      // per-case device statistics slots
+
+// statistics slots (FP64, per case)
+enum StatSlot {
+    ST_SUM_C = 0, ST_SUM_HE, ST_SUM_FL_DROP, ST_N_DROP, ST_Q_L, ST_T, ST_T_FREEZE,
+    ST_POT_RESID, ST_POT_CYCLES, ST_NONFINITE, ST_QL_PREV, ST_POT_DONE, ST_B2, ST_STEP,
+    ST_POT_FAIL, ST_SPARE
+};
+
+// Physical and numerical parameters of one case, resolved on the host in FP64.
+struct CaseParams {
+    int nx, ny, pitch;          // cells and row pitch (elements)
+    int periodic_x, periodic_y;
+    int thermal_dir[4];         // 1: Dirichlet temperature wall
+    int mag_dir[4];             // 1: Dirichlet potential wall
+    int solve_potential;        // 0: chi == 0 or no Dirichlet wall -> phi fixed
+    double wall_T[4];
+    double rho_l, rho_g, rho_s, mu_l, mu_g, mu_s, cp_l, cp_g, cp_s;
+    double lam_l, lam_g, lam_s, chi_l, chi_g, chi_s;
+    double beta, kappa, mobility, Q_g, gravity, T_m, L;
+    double dt, dts, cp_ref, vol_ratio, H0, cos_t, sin_t;
+};
+
+struct MGLevel {
+    int nx, ny, pitch;
+    void* mu;   // cell coefficient mu_m (M precision)
+    void* e;    // correction
+    void* r;    // right-hand side / residual
+};
+
+// Everything the kernels need to know about one case.
+struct DevCase {
+    CaseParams P;
+    // state sets: 0 = W^n (and W^{n+1}), 1 and 2 = Runge-Kutta stage buffers
+    void* He[3];      // HR precision (FP64 in both modes)
+    void* p[3];       // R precision
+    void* mx[3];
+    void* my[3];
+    void* C[3];
+    void* phi;        // R copy of the potential read by the stage kernel
+    double* phi64;    // FP64 master potential (== phi in FP64 mode)
+    void* Fs_prev;    // R
+    int nlev;
+    MGLevel lev[kMaxLevels];
+    double* red;      // stage-tile partial sums, kRedN per tile
+    int red_tiles;    // number of stage tiles of this case
+    double* mg_red;   // potential residual partial sums, 2 per fine tile
+    int mg_tiles;
+    double* stats;    // kStatN FP64 slots
+};
+
+struct TileRef {
+    int case_id, x0, y0, slot;
+};
+
+// ---------------------------------------------------------------------------
+// D2Q9 (Eq. 14, Fig. 1) with the textbook weights 4/9, 1/9, 1/36.
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr int d2q9_ex(int a) {
+    return a == 1 || a == 5 || a == 8 ? 1 : (a == 3 || a == 6 || a == 7 ? -1 : 0);
+}
+__host__ __device__ constexpr int d2q9_ey(int a) {
+    return a == 2 || a == 5 || a == 6 ? 1 : (a == 4 || a == 7 || a == 8 ? -1 : 0);
+}
+__host__ __device__ constexpr double d2q9_w(int a) {
+    return a == 0 ? 4.0 / 9.0 : (a <= 4 ? 1.0 / 9.0 : 1.0 / 36.0);
+}
+
+// Eq. 11 mixture: F_s g_s + (1 - F_s) C g_l + (1 - F_s)(1 - C) g_g
+template <class R>
+__device__ __forceinline__ R mixture(R Fs, R C, double gs, double gl, double gg) {
+    R liq = R(gg) + C * (R(gl) - R(gg));
+    return liq + Fs * (R(gs) - liq);
+}
+
+// Eq. 8 with T_s = T_l = T_m, H_es = C_p,s T_m, H_el = C_p,L(C) T_m + L, phase change
+// only where C >= 1/2.  The differences against the thresholds are formed in the
+// enthalpy's storage precision HR (FP64), the rest in R.
+template <class R, class HR>
+__device__ __forceinline__ void invert_enthalpy(const CaseParams& P, HR He, R C, R& T, R& Fl) {
+    R cpL = R(P.cp_g) + C * (R(P.cp_l) - R(P.cp_g));
+    HR Hes = HR(P.cp_s) * HR(P.T_m);
+    HR Hel = HR(cpL) * HR(P.T_m) + HR(P.L);
+    if (C < R(0.5)) {
+        Fl = R(1);
+        T = R(P.T_m) + R(He - Hel) / cpL;
+    } else if (He < Hes) {
+        Fl = R(0);
+        T = R(He) / R(P.cp_s);
+    } else if (He <= Hel) {
+        Fl = R(He - Hes) / R(Hel - Hes);
+        T = R(P.T_m);
+    } else {
+        Fl = R(1);
+        T = R(P.T_m) + R(He - Hel) / cpL;
+    }
+}
+
+template <class R>
+__device__ __forceinline__ R load(const void* base, size_t idx) {
+    return static_cast<const R*>(base)[idx];
+}
+
+}  // namespace lbfs

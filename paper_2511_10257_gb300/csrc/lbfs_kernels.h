@@ -1,0 +1,52 @@
+// lbfs_kernels.h -- launch entry points of the device kernels (host-side declarations).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "lbfs_internal.cuh"
+
+namespace lbfs {
+
+// stage kernel (lbfs_stage.cu); prec 0 = FP64, 1 = mixed
+int stage_tile_w(int prec, int tile);
+int stage_tile_h(int prec, int tile);
+cudaError_t launch_stage(int prec, int tile, const DevCase* cases, const TileRef* tiles, int ntiles,
+                         int stage, cudaStream_t st);
+
+// potential multigrid (lbfs_potential.cu).  MG tiles are 32 x 8 cells of one level.
+constexpr int kMgTX = 32, kMgTY = 8;
+cudaError_t launch_mg_restrict_mu(int prec, const DevCase* cases, const TileRef* tiles, int n,
+                                  int level_coarse, cudaStream_t st);
+cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* tiles, int n,
+                                 cudaStream_t st);
+cudaError_t launch_mg_finalize(const DevCase* cases, const int* case_ids, int ncases, double tol,
+                               int first, int* not_done, cudaStream_t st);
+cudaError_t launch_mg_smooth(int prec, const DevCase* cases, const TileRef* tiles, int n, int level,
+                             int color, cudaStream_t st);
+cudaError_t launch_mg_restrict_resid(int prec, const DevCase* cases, const TileRef* tiles, int n,
+                                     int level_coarse, cudaStream_t st);
+cudaError_t launch_mg_prolong(int prec, const DevCase* cases, const TileRef* tiles, int n, int level,
+                              cudaStream_t st);
+cudaError_t launch_mg_coarsest(int prec, const DevCase* cases, const int* case_ids, int ncases,
+                               int max_cells, cudaStream_t st);
+cudaError_t launch_mg_correct(int prec, const DevCase* cases, const TileRef* tiles, int n,
+                              cudaStream_t st);
+size_t mg_coarsest_smem(int prec, int max_cells);
+
+// per-case utility kernels (lbfs_fields.cu)
+struct InitArgs {
+    int kind;
+    double radius, cx, cy, T_init, xi;
+};
+cudaError_t launch_init(int prec, const DevCase* dcase, int nx, int ny, InitArgs a, cudaStream_t st);
+cudaError_t launch_mu_from_state(int prec, const DevCase* dcase, int nx, int ny, cudaStream_t st);
+cudaError_t launch_derive_fields(int prec, const DevCase* dcase, int nx, int ny, uint32_t mask,
+                                 double* out, cudaStream_t st);
+cudaError_t launch_store_fields(int prec, const DevCase* dcase, int nx, int ny, uint32_t mask,
+                                const double* in, cudaStream_t st);
+cudaError_t launch_stats_init(int prec, const DevCase* dcase, int nx, int ny, cudaStream_t st);
+cudaError_t launch_step_finalize(const DevCase* cases, const int* case_ids, int ncases,
+                                 cudaStream_t st);
+
+}  // namespace lbfs

@@ -1,0 +1,496 @@
+// lbfs_stage.cu -- one Runge-Kutta stage of the LBFS finite-volume update, fused per
+// tile: load the stage state with a three-cell halo into shared memory, derive the
+// cell quantities (Eq. 8 inversion, Eq. 11 mixture, velocity, mu_c, |H|^2), build
+// every face flux of the tile by the LBFS reconstruction (Eqs. 44, 45, 20, 28, 29,
+// 22, 32, 33, 43), add the sources (Eq. 41), form R(W) (Eq. 42) and the SSP-RK3
+// combination, and write the next stage.  The last stage also applies the step-end
+// rest condition of the solid, stores F_s^n for the next step's dF_s/dt, writes the
+// potential coefficient mu_m for the next solve, and reduces the diagnostics.
+#include <cstdio>
+
+#include "lbfs_internal.cuh"
+#include "lbfs_kernels.h"
+
+namespace lbfs {
+
+enum { SP = 0, SU, SV, SC, ST, SHE, SFS, SRHO, SMU, SPHI, SH2, NSH };
+
+template <int TX, int TY>
+struct Geom {
+    static constexpr int H = 3;
+    static constexpr int RW = TX + 2 * H, RH = TY + 2 * H, RN = RW * RH;
+    static constexpr int NFX = (TX + 1) * TY, NFY = TX * (TY + 1), NF = NFX + NFY;
+};
+
+// Per-face flux by the LBFS reconstruction, in the face frame (n normal, t
+// tangential).  Cells A (lower/left) and B (upper/right) at region indices kA, kB;
+// sn and st are the region strides along n and t.  Uses, for X = h, g and the
+// f^{eq-m} form of f, X*_a = (3/2 - tau) X_eq,a(x_f) + (tau - 1/2) X_eq,a(x - e_a dts),
+// which is Eqs. 16, 22, 32, 33 with X_neq = -tau (X_eq(x_f) - X_eq(x - e_a dts)),
+// and the D2Q9 moment identities for the interface equilibria.
+template <class R>
+__device__ __forceinline__ void face_flux(const CaseParams& P, const R* __restrict__ s, int RN,
+                                          int kA, int kB, int sn, int st, bool xface,
+                                          R& Fh, R& Fp, R& Fmn, R& Fmt, R& Fc) {
+    const int fun = xface ? SU : SV, fut = xface ? SV : SU;
+    const int qf[7] = {SP, fun, fut, SC, SMU, ST, SHE};
+    R vA[7], nA[7], tA[7], vB[7], nB[7], tB[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) {
+        const R* f = s + qf[q] * RN;
+        vA[q] = f[kA];
+        nA[q] = R(0.5) * (f[kA + sn] - f[kA - sn]);
+        tA[q] = R(0.5) * (f[kA + st] - f[kA - st]);
+        vB[q] = f[kB];
+        nB[q] = R(0.5) * (f[kB + sn] - f[kB - sn]);
+        tB[q] = R(0.5) * (f[kB + st] - f[kB - st]);
+    }
+    const R FsA = s[SFS * RN + kA], FsB = s[SFS * RN + kB];
+    const R dts = R(P.dts);
+    const R cpref = R(P.cp_ref), Qg = R(P.Q_g);
+    R Sp = 0, Sjn = 0, Sjt = 0, SC_ = 0, SH = 0, Ah = 0, Ag = 0;
+    R Bpn = 0, Bpt = 0, BGn = 0, BGt = 0;
+#pragma unroll
+    for (int a = 0; a < 9; ++a) {
+        const int en = d2q9_ex(a), et = d2q9_ey(a);
+        const R w = R(d2q9_w(a));
+        R q[7];
+        R Fs;
+        const R ot = -R(et) * dts;
+        if (en > 0) {
+            const R on = R(0.5) - dts;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) q[k] = vA[k] + on * nA[k] + ot * tA[k];
+            Fs = FsA;
+        } else if (en < 0) {
+            const R on = R(-0.5) + dts;
+#pragma unroll
+            for (int k = 0; k < 7; ++k) q[k] = vB[k] + on * nB[k] + ot * tB[k];
+            Fs = FsB;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 7; ++k)
+                q[k] = R(0.5) * ((vA[k] + R(0.5) * nA[k] + ot * tA[k]) +
+                                 (vB[k] - R(0.5) * nB[k] + ot * tB[k]));
+            Fs = R(0.5) * (FsA + FsB);
+        }
+        const R p = q[0], un = q[1], ut = q[2], C = q[3], mu = q[4], T = q[5], He = q[6];
+        const R rho = mixture(Fs, C, P.rho_s, P.rho_l, P.rho_g);
+        const R cp = mixture(Fs, C, P.cp_s, P.cp_l, P.cp_g);
+        const R eu = R(en) * un + R(et) * ut;
+        const R uu = un * un + ut * ut;
+        const R G = R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu;   // Gamma_a(u)
+        const R feq = w * (p + rho * G * R(1.0 / 3.0));
+        R geq, heq;
+        if (a == 0) {
+            geq = C - R(5.0 / 3.0) * mu * Qg;
+            heq = He - cpref * T + w * (cpref * T - R(1.5) * cp * T * uu);
+        } else {
+            geq = R(3) * w * (mu * Qg + C * eu);
+            heq = w * (cpref * T + cp * T * G);
+        }
+        Sp += feq;
+        Sjn += R(en) * feq;
+        Sjt += R(et) * feq;
+        SC_ += geq;
+        SH += heq;
+        if (en != 0) {
+            Ah += R(en) * heq;
+            Ag += R(en) * geq;
+            Bpn += w * p;                 // en * en = 1
+            BGn += w * G;
+            if (et != 0) {
+                Bpt += R(en * et) * w * p;
+                BGt += R(en * et) * w * G;
+            }
+        }
+    }
+    // Eq. 45: interface values
+    const R Fsf = R(0.5) * (FsA + FsB);
+    const R Cf = SC_, pf = Sp, Hef = SH;
+    const R rhof = mixture(Fsf, Cf, P.rho_s, P.rho_l, P.rho_g);
+    const R inv_rc = R(3) / rhof;                 // 1 / (rho_f c_s^2)
+    const R ufn = Sjn * inv_rc, uft = Sjt * inv_rc;
+    const R cpf = mixture(Fsf, Cf, P.cp_s, P.cp_l, P.cp_g);
+    const R lamf = mixture(Fsf, Cf, P.lam_s, P.lam_l, P.lam_g);
+    const R muf = mixture(Fsf, Cf, P.mu_s, P.mu_l, P.mu_g);
+    R Tf, Flf;
+    invert_enthalpy<R, R>(P, Hef, Cf, Tf, Flf);
+    const R tau_f = R(0.5) + muf * inv_rc / dts;
+    const R tau_h = R(0.5) + lamf * inv_rc / (cpref * dts);
+    const R tau_g = R(0.5) + R(P.mobility) / (Qg * dts);
+    const R c3 = R(1.0 / 3.0);
+    Fh = (R(1.5) - tau_h) * cpf * Tf * ufn + (tau_h - R(0.5)) * Ah;
+    Fc = (R(1.5) - tau_g) * Cf * ufn + (tau_g - R(0.5)) * Ag;
+    Fp = Sjn;
+    Fmn = (R(1.5) - tau_f) * c3 * (pf + rhof * ufn * ufn) + (tau_f - R(0.5)) * (Bpn + rhof * c3 * BGn);
+    Fmt = (R(1.5) - tau_f) * c3 * rhof * ufn * uft + (tau_f - R(0.5)) * (Bpt + rhof * c3 * BGt);
+}
+
+// Wall face (no-slip, no-flux): momentum flux c_s^2 (p n - mu du_t/dn) with the wall
+// half a cell from the inner centre; enthalpy flux -(lambda/rho) dT/dn on Dirichlet
+// walls, zero on adiabatic ones; no mass or phase-field flux.
+template <class R>
+__device__ __forceinline__ void wall_flux(const CaseParams& P, const R* __restrict__ s, int RN,
+                                          int k, int wall, R F[5]) {
+    const R Fs = s[SFS * RN + k], C = s[SC * RN + k];
+    const R rho = s[SRHO * RN + k];
+    const R mu = mixture(Fs, C, P.mu_s, P.mu_l, P.mu_g);
+    const R lam = mixture(Fs, C, P.lam_s, P.lam_l, P.lam_g);
+    const R side = (wall == 0 || wall == 2) ? R(1) : R(-1);
+    const R ut = wall < 2 ? s[SV * RN + k] : s[SU * RN + k];
+    const R dut = side * ut * R(2);
+    const R dT = side * (s[ST * RN + k] - R(P.wall_T[wall])) * R(2);
+    const R c3 = R(1.0 / 3.0);
+    F[1] = R(0);
+    F[4] = R(0);
+    if (wall < 2) {
+        F[2] = c3 * s[SP * RN + k];
+        F[3] = c3 * (-mu * dut);
+    } else {
+        F[3] = c3 * s[SP * RN + k];
+        F[2] = c3 * (-mu * dut);
+    }
+    F[0] = P.thermal_dir[wall] ? -(lam / rho) * dT : R(0);
+}
+
+template <class R, class HR, int TX, int TY, int NT>
+__global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ cases,
+                                                   const TileRef* __restrict__ tiles, int stage) {
+    using Gm = Geom<TX, TY>;
+    constexpr int RW = Gm::RW, RH = Gm::RH, RN = Gm::RN, NFX = Gm::NFX, NF = Gm::NF;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    R* s = reinterpret_cast<R*>(smem_raw);
+    R* flux = s + NSH * RN;                                         // [5][NF]
+    signed char* kind = reinterpret_cast<signed char*>(flux + 5 * NF);  // [RN]
+    __shared__ CaseParams P;
+    __shared__ double red_s[32][kRedN];
+
+    const TileRef tr = tiles[blockIdx.x];
+    const DevCase* dc = cases + tr.case_id;
+    {
+        const int* src = reinterpret_cast<const int*>(&dc->P);
+        int* dst = reinterpret_cast<int*>(&P);
+        for (int i = threadIdx.x; i < (int)(sizeof(CaseParams) / sizeof(int)); i += NT) dst[i] = src[i];
+    }
+    const int in = stage == 0 ? 0 : (stage == 1 ? 1 : 2);
+    const int out = stage == 0 ? 1 : (stage == 1 ? 2 : 0);
+    const HR* __restrict__ gHe = static_cast<const HR*>(dc->He[in]);
+    const R* __restrict__ gP = static_cast<const R*>(dc->p[in]);
+    const R* __restrict__ gMx = static_cast<const R*>(dc->mx[in]);
+    const R* __restrict__ gMy = static_cast<const R*>(dc->my[in]);
+    const R* __restrict__ gC = static_cast<const R*>(dc->C[in]);
+    const R* __restrict__ gPhi = static_cast<const R*>(dc->phi);
+    __syncthreads();
+    const int nx = P.nx, ny = P.ny, pitch = P.pitch;
+    const int x0 = tr.x0, y0 = tr.y0;
+
+    // ---- phase 1: load the stage state with halo, ghost rules at walls ----------
+    for (int k = threadIdx.x; k < RN; k += NT) {
+        const int lx = k % RW, ly = k / RW;
+        const int gx = x0 - Gm::H + lx, gy = y0 - Gm::H + ly;
+        int sx, sy, xs, ys;  // source cell and status: 0 inside, 1 ghost low, 2 ghost high, 3 far
+        if (P.periodic_x) {
+            sx = ((gx % nx) + nx) % nx;
+            xs = 0;
+        } else if (gx >= 0 && gx < nx) {
+            sx = gx; xs = 0;
+        } else if (gx == -1) {
+            sx = 0; xs = 1;
+        } else if (gx == nx) {
+            sx = nx - 1; xs = 2;
+        } else {
+            sx = gx < 0 ? 0 : nx - 1; xs = 3;
+        }
+        if (P.periodic_y) {
+            sy = ((gy % ny) + ny) % ny;
+            ys = 0;
+        } else if (gy >= 0 && gy < ny) {
+            sy = gy; ys = 0;
+        } else if (gy == -1) {
+            sy = 0; ys = 1;
+        } else if (gy == ny) {
+            sy = ny - 1; ys = 2;
+        } else {
+            sy = gy < 0 ? 0 : ny - 1; ys = 3;
+        }
+        int wall = -1;
+        signed char kd;
+        if (xs == 0 && ys == 0) {
+            kd = 0;
+        } else if ((xs == 1 || xs == 2) && ys == 0) {
+            wall = xs - 1;
+            kd = (signed char)(1 + wall);
+        } else if (xs == 0 && (ys == 1 || ys == 2)) {
+            wall = 2 + ys - 1;
+            kd = (signed char)(1 + wall);
+        } else {
+            kd = 5;
+        }
+        const size_t gi = (size_t)sy * pitch + sx;
+        const HR He = gHe[gi];
+        const R C = gC[gi];
+        R T, Fl;
+        invert_enthalpy<R, HR>(P, He, C, T, Fl);
+        const R Fs = R(1) - Fl;
+        const R rho = mixture(Fs, C, P.rho_s, P.rho_l, P.rho_g);
+        R u = gMx[gi] * R(3) / rho, v = gMy[gi] * R(3) / rho;
+        R phi = gPhi[gi];
+        R Hes = R(He);
+        if (wall >= 0) {
+            u = -u;
+            v = -v;
+            if (P.thermal_dir[wall]) T = R(2) * R(P.wall_T[wall]) - T;
+            const R cp = mixture(Fs, C, P.cp_s, P.cp_l, P.cp_g);
+            Hes = cp * T + R(P.L) * (R(1) - Fs);
+            if (P.mag_dir[wall]) {
+                double wx = wall == 0 ? 0.0 : (wall == 1 ? (double)nx : sx + 0.5);
+                double wy = wall == 2 ? 0.0 : (wall == 3 ? (double)ny : sy + 0.5);
+                double pw = -P.H0 * (wx * P.cos_t + wy * P.sin_t);
+                phi = R(2.0 * pw) - phi;
+            }
+        }
+        s[SP * RN + k] = gP[gi];
+        s[SU * RN + k] = u;
+        s[SV * RN + k] = v;
+        s[SC * RN + k] = C;
+        s[ST * RN + k] = T;
+        s[SHE * RN + k] = Hes;
+        s[SFS * RN + k] = Fs;
+        s[SRHO * RN + k] = rho;
+        s[SPHI * RN + k] = phi;
+        kind[k] = kd;
+    }
+    __syncthreads();
+    // ---- phase 2: mu_c and |H|^2 at inner cells -------------------------------
+    const R beta = R(P.beta), kappa = R(P.kappa);
+    for (int k = threadIdx.x; k < RN; k += NT) {
+        const int lx = k % RW, ly = k / RW;
+        R mu = 0, h2 = 0;
+        if (kind[k] == 0 && lx > 0 && lx < RW - 1 && ly > 0 && ly < RH - 1) {
+            const R* c = s + SC * RN;
+            const R C = c[k];
+            const R lap = c[k + 1] + c[k - 1] + c[k + RW] + c[k - RW] - R(4) * C;
+            mu = R(2) * beta * C * (C - R(1)) * (R(2) * C - R(1)) - kappa * lap;
+            const R* ph = s + SPHI * RN;
+            const R hx = R(-0.5) * (ph[k + 1] - ph[k - 1]);
+            const R hy = R(-0.5) * (ph[k + RW] - ph[k - RW]);
+            h2 = hx * hx + hy * hy;
+        }
+        s[SMU * RN + k] = mu;
+        s[SH2 * RN + k] = h2;
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < RN; k += NT) {
+        const int kd = kind[k];
+        if (kd >= 1 && kd <= 4) {
+            const int lx = k % RW, ly = k / RW;
+            const int w = kd - 1;
+            int ks = k + (w == 0 ? 1 : w == 1 ? -1 : w == 2 ? RW : -RW);
+            const int sx = ks % RW, sy = ks / RW;
+            if (sx > 0 && sx < RW - 1 && sy > 0 && sy < RH - 1 && lx >= 0 && ly >= 0) {
+                s[SMU * RN + k] = s[SMU * RN + ks];
+                s[SH2 * RN + k] = s[SH2 * RN + ks];
+            }
+        }
+    }
+    __syncthreads();
+    // ---- phase 3: face fluxes ------------------------------------------------------
+    for (int f = threadIdx.x; f < NF; f += NT) {
+        R F[5] = {0, 0, 0, 0, 0};
+        if (f < NFX) {
+            const int fx = f % (TX + 1), ty = f / (TX + 1);
+            const int gxf = x0 + fx, gy = y0 + ty;
+            if (gy < ny && gxf <= nx) {
+                const int kB = (ty + Gm::H) * RW + fx + Gm::H, kA = kB - 1;
+                if (!P.periodic_x && gxf == 0) {
+                    wall_flux<R>(P, s, RN, kB, 0, F);
+                } else if (!P.periodic_x && gxf == nx) {
+                    wall_flux<R>(P, s, RN, kA, 1, F);
+                } else {
+                    face_flux<R>(P, s, RN, kA, kB, 1, RW, true, F[0], F[1], F[2], F[3], F[4]);
+                }
+            }
+        } else {
+            const int g = f - NFX;
+            const int tx = g % TX, fy = g / TX;
+            const int gx = x0 + tx, gyf = y0 + fy;
+            if (gx < nx && gyf <= ny) {
+                const int kB = (fy + Gm::H) * RW + tx + Gm::H, kA = kB - RW;
+                if (!P.periodic_y && gyf == 0) {
+                    wall_flux<R>(P, s, RN, kB, 2, F);
+                } else if (!P.periodic_y && gyf == ny) {
+                    wall_flux<R>(P, s, RN, kA, 3, F);
+                } else {
+                    face_flux<R>(P, s, RN, kA, kB, RW, 1, false, F[0], F[1], F[3], F[2], F[4]);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 5; ++c) flux[c * NF + f] = F[c];
+    }
+    __syncthreads();
+    // ---- phase 4: R(W), sources, Runge-Kutta combination ------------------------
+    const R c3 = R(1.0 / 3.0);
+    const double a_rk = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
+    const double b_rk = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+    const R dt = R(P.dt);
+    double acc[kRedN] = {0, 0, 0, 0, 0, 0};
+    HR* oHe = static_cast<HR*>(dc->He[out]);
+    R* oP = static_cast<R*>(dc->p[out]);
+    R* oMx = static_cast<R*>(dc->mx[out]);
+    R* oMy = static_cast<R*>(dc->my[out]);
+    R* oC = static_cast<R*>(dc->C[out]);
+    const HR* bHe = static_cast<const HR*>(dc->He[0]);
+    const R* bP = static_cast<const R*>(dc->p[0]);
+    const R* bMx = static_cast<const R*>(dc->mx[0]);
+    const R* bMy = static_cast<const R*>(dc->my[0]);
+    const R* bC = static_cast<const R*>(dc->C[0]);
+    R* Fsp = static_cast<R*>(dc->Fs_prev);
+    for (int c = threadIdx.x; c < TX * TY; c += NT) {
+        const int tx = c % TX, ty = c / TX;
+        const int gx = x0 + tx, gy = y0 + ty;
+        if (gx >= nx || gy >= ny) continue;
+        const int k = (ty + Gm::H) * RW + tx + Gm::H;
+        const int fl = ty * (TX + 1) + tx, fb = NFX + ty * TX + tx;
+        R Rw[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q)
+            Rw[q] = -(flux[q * NF + fl + 1] - flux[q * NF + fl]) -
+                    (flux[q * NF + fb + TX] - flux[q * NF + fb]);
+        const R Fs = s[SFS * RN + k], C = s[SC * RN + k], T = s[ST * RN + k];
+        const R u = s[SU * RN + k], v = s[SV * RN + k], rho = s[SRHO * RN + k];
+        const R cp = mixture(Fs, C, P.cp_s, P.cp_l, P.cp_g);
+        const R chi = mixture(Fs, C, P.chi_s, P.chi_l, P.chi_g);
+        const R divu = R(0.5) * (s[SU * RN + k + 1] - s[SU * RN + k - 1]) +
+                       R(0.5) * (s[SV * RN + k + RW] - s[SV * RN + k - RW]);
+        const R drx = R(0.5) * (s[SRHO * RN + k + 1] - s[SRHO * RN + k - 1]);
+        const R dry = R(0.5) * (s[SRHO * RN + k + RW] - s[SRHO * RN + k - RW]);
+        const R dhx = R(0.5) * (s[SH2 * RN + k + 1] - s[SH2 * RN + k - 1]);
+        const R dhy = R(0.5) * (s[SH2 * RN + k + RW] - s[SH2 * RN + k - RW]);
+        const R dmx = R(0.5) * (s[SMU * RN + k + 1] - s[SMU * RN + k - 1]);
+        const R dmy = R(0.5) * (s[SMU * RN + k + RW] - s[SMU * RN + k - RW]);
+        const size_t gi = (size_t)gy * pitch + gx;
+        // W^n at this cell and the lagged dF_s/dt
+        const HR He0 = bHe[gi];
+        const R C0 = bC[gi];
+        R T0, Fl0;
+        invert_enthalpy<R, HR>(P, He0, C0, T0, Fl0);
+        const R Fs_n = R(1) - Fl0;
+        const R Sd = (Fs_n - Fsp[gi]) / dt;
+        const R vr = R(P.vol_ratio);
+        Rw[0] += cp * T * divu;
+        Rw[1] += u * c3 * drx + v * c3 * dry + rho * c3 * vr * Sd;
+        Rw[2] += c3 * (-C * dmx + R(0.5) * chi * dhx - rho * u * Sd);
+        Rw[3] += c3 * (-C * dmy + R(0.5) * chi * dhy + rho * R(P.gravity) - rho * v * Sd);
+        Rw[4] += C * vr * Sd;
+        // stage input at this cell
+        const HR Hek = gHe[gi];
+        const R pk = gP[gi], mxk = gMx[gi], myk = gMy[gi], Ck = gC[gi];
+        const HR aH = HR(a_rk), bH = HR(b_rk);
+        const R a = R(a_rk), b = R(b_rk);
+        HR Hen;
+        R pn, mxn, myn, Cn;
+        if (stage == 0) {
+            Hen = Hek + HR(dt) * HR(Rw[0]);
+            pn = pk + dt * Rw[1];
+            mxn = mxk + dt * Rw[2];
+            myn = myk + dt * Rw[3];
+            Cn = Ck + dt * Rw[4];
+        } else {
+            Hen = aH * He0 + bH * (Hek + HR(dt) * HR(Rw[0]));
+            pn = a * bP[gi] + b * (pk + dt * Rw[1]);
+            mxn = a * bMx[gi] + b * (mxk + dt * Rw[2]);
+            myn = a * bMy[gi] + b * (myk + dt * Rw[3]);
+            Cn = a * C0 + b * (Ck + dt * Rw[4]);
+        }
+        if (stage == 2) {
+            // step end: solid held at rest, (rho u) <- (1 - F_s)(rho u)
+            R Tn, Fln;
+            invert_enthalpy<R, HR>(P, Hen, Cn, Tn, Fln);
+            mxn *= Fln;
+            myn *= Fln;
+            Fsp[gi] = Fs_n;
+            const R Fsn = R(1) - Fln;
+            R* mu0 = static_cast<R*>(dc->lev[0].mu);
+            mu0[(size_t)gy * dc->lev[0].pitch + gx] = R(1) + mixture(Fsn, Cn, P.chi_s, P.chi_l, P.chi_g);
+            acc[0] += (double)Cn;
+            acc[1] += (double)Hen;
+            if (Cn >= R(0.5)) {
+                acc[2] += (double)Fln;
+                acc[3] += 1.0;
+                acc[4] += (double)Fsn;
+            }
+            const bool fin = isfinite((double)Hen) && isfinite((double)pn) && isfinite((double)mxn) &&
+                             isfinite((double)myn) && isfinite((double)Cn);
+            if (!fin) acc[5] += 1.0;
+        }
+        oHe[gi] = Hen;
+        oP[gi] = pn;
+        oMx[gi] = mxn;
+        oMy[gi] = myn;
+        oC[gi] = Cn;
+    }
+    if (stage == 2) {
+        // block reduction of the diagnostics (FP64, fixed order)
+        const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+        for (int q = 0; q < kRedN; ++q) {
+            double v = acc[q];
+            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+            if (lane == 0) red_s[wid][q] = v;
+        }
+        __syncthreads();
+        if (threadIdx.x < kRedN) {
+            double v = 0.0;
+            for (int w = 0; w < NT / 32; ++w) v += red_s[w][threadIdx.x];
+            dc->red[(size_t)tr.slot * kRedN + threadIdx.x] = v;
+        }
+    }
+}
+
+// ---- launch helpers ------------------------------------------------------------
+template <class R, class HR, int TX, int TY>
+struct StageCfg {
+    static constexpr int NT = ((2 * TX * TY + TX + TY) / 2 + 31) / 32 * 32;
+    static constexpr size_t smem() {
+        using Gm = Geom<TX, TY>;
+        return (size_t)(NSH * Gm::RN + 5 * Gm::NF) * sizeof(R) + Gm::RN + 16;
+    }
+};
+
+template <class R, class HR, int TX, int TY>
+static cudaError_t launch_stage_t(const DevCase* cases, const TileRef* tiles, int ntiles, int stage,
+                                  cudaStream_t st) {
+    using Cf = StageCfg<R, HR, TX, TY>;
+    auto kern = stage_kernel<R, HR, TX, TY, Cf::NT>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)Cf::smem());
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    kern<<<ntiles, Cf::NT, Cf::smem(), st>>>(cases, tiles, stage);
+    return cudaGetLastError();
+}
+
+int stage_tile_w(int prec, int tile) {
+    (void)prec;
+    (void)tile;
+    return 32;
+}
+int stage_tile_h(int prec, int tile) {
+    (void)tile;
+    return prec == 0 ? 8 : 8;
+}
+
+cudaError_t launch_stage(int prec, int tile, const DevCase* cases, const TileRef* tiles, int ntiles,
+                         int stage, cudaStream_t st) {
+    (void)tile;
+    if (ntiles <= 0) return cudaSuccess;
+    if (prec == 0) return launch_stage_t<double, double, 32, 8>(cases, tiles, ntiles, stage, st);
+    return launch_stage_t<float, double, 32, 8>(cases, tiles, ntiles, stage, st);
+}
+
+}  // namespace lbfs

@@ -142,13 +142,13 @@ def random_state(nx: int, ny: int, seed: int, latent: float = 10.0, amp_u: float
     rng = np.random.default_rng(seed)
     sm = lambda: _smooth_field(rng, nx, ny)
     wn = lambda: rng.uniform(-1, 1, size=(ny, nx)) if noise > 0 else 0.0
-    C = 0.5 + 0.55 * sm() + noise * wn()
-    He = 0.5 * latent + (0.5 * latent + 0.6) * sm() * 1.6 + noise * latent * wn()
-    p = 0.01 * sm() + 0.01 * noise * wn()
-    mx = amp_u * sm() + amp_u * noise * wn()
-    my = amp_u * sm() + amp_u * noise * wn()
-    Fs_prev = np.clip(0.5 + 0.6 * sm(), 0.0, 1.0)
-    x = (np.arange(nx) + 0.5)[None, :]
-    y = (np.arange(ny) + 0.5)[:, None]
-    phi = -0.01 * (0.3 * x + 0.7 * y) + 0.001 * sm()
-    return {HE: He, P: p, MX: mx, MY: my, C: C, FSPREV: Fs_prev, PHI: phi}
+    c_f = 0.5 + 0.55 * sm() + noise * wn()
+    he_f = 0.5 * latent + (0.5 * latent + 0.6) * sm() * 1.6 + noise * latent * wn()
+    p_f = 0.01 * sm() + 0.01 * noise * wn()
+    mx_f = amp_u * sm() + amp_u * noise * wn()
+    my_f = amp_u * sm() + amp_u * noise * wn()
+    fs_f = np.clip(0.5 + 0.6 * sm(), 0.0, 1.0)
+    xs = (np.arange(nx) + 0.5)[None, :]
+    ys = (np.arange(ny) + 0.5)[:, None]
+    phi_f = -0.01 * (0.3 * xs + 0.7 * ys) + 0.001 * sm()
+    return {HE: he_f, P: p_f, MX: mx_f, MY: my_f, C: c_f, FSPREV: fs_f, PHI: phi_f}

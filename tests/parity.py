@@ -1,0 +1,35 @@
+"""Helpers shared by the GPU parity tests: run the CUDA path and the CPU oracle on the
+same seeded inputs and compare field by field."""
+import numpy as np
+
+import oracle
+from paper_2511_10257_gb300 import inputs as I
+
+ALL_FIELDS = [I.PHI, I.HE, I.T, I.FL, I.P, I.U, I.V, I.C, I.MUC, I.RHO, I.MX, I.MY, I.FSPREV]
+
+
+# Liquid and solid fractions live on [0, 1]: their scale is 1 even when a case has
+# almost no solid (then the oracle's field is rounding noise of order 1e-16).
+SCALE_FLOOR = {I.FL: 1.0, I.FSPREV: 1.0}
+
+
+def rel_err(a, b, floor=1e-30):
+    """max |a - b| relative to the reference field's largest magnitude"""
+    return float(np.max(np.abs(a - b)) / max(float(np.max(np.abs(b))), floor))
+
+
+def compare(solver, case_id, ref, fields=ALL_FIELDS):
+    got = solver.fields(case_id, fields)
+    return {I.FIELD_NAMES[f]: rel_err(got[f], ref.get(f), SCALE_FLOOR.get(f, 1e-30)) for f in fields}
+
+
+def assert_parity(solver, case_id, ref, tol, fields=ALL_FIELDS):
+    errs = compare(solver, case_id, ref, fields)
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, f"fields beyond {tol:g}: {bad}"
+    return errs
+
+
+def set_both(solver, case_id, ref, state):
+    solver.set_fields(case_id, state)
+    ref.set_state(state)

@@ -276,3 +276,36 @@ def test_one_dimensional_reduction():
         a = o.get(f)
         assert np.max(np.abs(a - a[:1, :])) <= 1e-13 * max(np.max(np.abs(a)), 1e-30)
     assert np.max(np.abs(o.get(I.V))) <= 1e-18
+
+
+def _aspect(o, n):
+    """a/b of the drop from second moments of C (an ellipse has I_aa / I_bb = (a/b)^2)"""
+    Cf = np.clip(o.get(I.C), 0.0, 1.0)
+    x = np.arange(n) + 0.5
+    X, Y = np.meshgrid(x, x)
+    cx, cy = (Cf * X).sum() / Cf.sum(), (Cf * Y).sum() / Cf.sum()
+    return math.sqrt((Cf * (X - cx) ** 2).sum() / (Cf * (Y - cy) ** 2).sum())
+
+
+@pytest.mark.slow
+def test_ferrofluid_drop_small_deformation():
+    """Sec. 4.3: a free ferrofluid drop (chi = 2) in a uniform field along x elongates
+    along the field.  Minimising surface plus magnetic co-energy for an ellipse with
+    demagnetising factor b/(a+b) gives, to first order in Bo_m (diameter-based),
+    a/b - 1 = chi^2 Bo_m / (3 (2 + chi)^2).  The overdamped approach to the steady
+    shape is extrapolated (Aitken) from the last three samples; within 5 %."""
+    n, R, chi, bo = 64, 10.0, 2.0, 1.0
+    c = I.case(n, n, init=1, radius=R, drop_x=n / 2, drop_y=n / 2, T_init=1.0, bo_m=bo,
+               field_angle_deg=0.0, chi_l=chi, chi_s=chi, thermal_dirichlet=(0, 0, 0, 0),
+               mu_l=0.3, mu_s=0.3, mu_g=0.03)
+    o = oracle.Oracle(c, threads=4)
+    vals = []
+    for _ in range(10):
+        o.step(200)
+        vals.append(_aspect(o, n) - 1.0)
+    a, b, cc = vals[-3:]
+    d1, d2 = b - a, cc - b
+    assert d1 > 0 and 0 < d2 < d1
+    steady = cc + d2 * d2 / (d1 - d2)
+    expect = chi * chi * bo / (3.0 * (2.0 + chi) ** 2)
+    assert steady == pytest.approx(expect, rel=0.05)

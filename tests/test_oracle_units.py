@@ -213,3 +213,18 @@ def test_pressure_flux_is_compatibility_momentum():
     assert F[1] == pytest.approx((0.0 - 1e-3) / 6.0, rel=1e-12)
     F = o.face_flux(0, 1, 1)
     assert abs(F[1]) < 1e-18
+
+
+def test_random_states_cover_every_inversion_branch():
+    """The seeded parity inputs reach solid, mushy and liquid droplet cells and gas
+    cells, and the oracle steps them without producing non-finite values."""
+    st = I.random_state(16, 12, seed=3, latent=10.0, noise=0.05)
+    c = I.case(16, 12, stefan=0.0, latent=10.0, H0=0.02, radius=4.0)
+    o = oracle.Oracle(c)
+    o.set_state(st)
+    Fl, C = o.get(I.FL), o.get(I.C)
+    drop = C >= 0.5
+    assert np.any(Fl[drop] == 0.0) and np.any((Fl[drop] > 0) & (Fl[drop] < 1)) and np.any(Fl[drop] == 1.0)
+    assert np.any(~drop)
+    o.step(3)
+    assert o.stats()["nonfinite"] == 0
