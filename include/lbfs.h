@@ -166,6 +166,29 @@ enum { LBFS_TIMING_STAGE = 0, LBFS_TIMING_POTENTIAL = 1, LBFS_TIMING_FINALIZE = 
 lbfs_status lbfs_timing(lbfs_ctx* ctx, int32_t enable);
 lbfs_status lbfs_timing_read(lbfs_ctx* ctx, double* ms, int64_t* counts, int32_t n);
 
+/* Diagnostics of a state that lives in the caller's device memory, computed without
+ * allocating anything (the paper has no counterpart; it is a service for callers that
+ * cannot allocate device memory, e.g. code running inside another component's fixed
+ * memory pool or while that component records work, which must not call cudaMalloc).
+ *   desc:  the case; only nx, ny, cp_l, cp_g, cp_s, T_m, stefan/latent and wall_T[2]
+ *          are read (the Eq. 8 inversion).
+ *   d_He, d_C: device arrays of nx*ny FP64 values, row-major with x fastest (caller-owned).
+ *   d_out: device array of 5 FP64 values (caller-owned) receiving sum C, sum H_e,
+ *          sum F_l over droplet cells (C >= 1/2), the number of droplet cells and Q_L.
+ *   stream: cudaStream_t the two kernels run on (NULL: the legacy default stream); the
+ *          call returns once they are enqueued.
+ *   err, err_len: optional buffer for a message ("" on success).
+ * Scratch: one row of partial sums per grid row in a fixed 16384 x 5 FP64 device array
+ * (640 KiB) that every device using this library keeps until the process exits;
+ * ny > 16384 returns LBFS_EINVAL before any launch.  No cudaMalloc, cudaFree or other
+ * allocating call is made.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first call before
+ * any stream capture.  All calls share the array and every call rewrites the rows it
+ * uses, so nothing needs clearing, but calls whose kernels overlap on the GPU (other
+ * streams, other host threads) race on it: order them on one stream. */
+lbfs_status lbfs_state_stats_noalloc(const lbfs_case_desc* desc, const double* d_He, const double* d_C,
+                                     double* d_out, void* stream, char* err, size_t err_len);
+
 /* Release all device memory and the owned stream (if any). */
 void lbfs_destroy(lbfs_ctx* ctx);
 
