@@ -59,6 +59,7 @@ struct lbfs_ctx {
     int64_t launches = 0;
     double mg_tol = 0.0;
     int mg_max_cycles = 0;
+    int half = 0;          // every defined case has dts = 1/2
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
     // kernel timing (events on the context stream)
@@ -223,6 +224,20 @@ lbfs_status resolve(lbfs_ctx* ctx, const lbfs_case_desc& d, CaseParams& P) {
     return LBFS_OK;
 }
 
+template <class R>
+void fill_phys(const CaseParams& P, PhysT<R>& q) {
+    q.rho_s = R(P.rho_s); q.rho_l = R(P.rho_l); q.rho_g = R(P.rho_g);
+    q.mu_s = R(P.mu_s); q.mu_l = R(P.mu_l); q.mu_g = R(P.mu_g);
+    q.lam_s = R(P.lam_s); q.lam_l = R(P.lam_l); q.lam_g = R(P.lam_g);
+    q.cp_s = R(P.cp_s); q.cp_l = R(P.cp_l); q.cp_g = R(P.cp_g);
+    q.chi_s = R(P.chi_s); q.chi_l = R(P.chi_l); q.chi_g = R(P.chi_g);
+    q.beta = R(P.beta); q.kappa = R(P.kappa); q.Q_g = R(P.Q_g); q.cp_ref = R(P.cp_ref);
+    q.dts = R(P.dts); q.inv_dts = R(1.0 / P.dts); q.inv_cpref_dts = R(1.0 / (P.cp_ref * P.dts));
+    q.tau_g = R(0.5 + P.mobility / (P.Q_g * P.dts));
+    q.dt = R(P.dt); q.vol_ratio = R(P.vol_ratio); q.gravity = R(P.gravity); q.T_m = R(P.T_m); q.L = R(P.L);
+    for (int w = 0; w < 4; ++w) q.wall_T[w] = R(P.wall_T[w]);
+}
+
 // Upload the concatenated tile lists of all defined cases.
 lbfs_status rebuild(lbfs_ctx* ctx) {
     drop_graph(ctx);
@@ -230,10 +245,12 @@ lbfs_status rebuild(lbfs_ctx* ctx) {
     std::vector<TileRef> st;
     std::vector<int> act, pot;
     int depth = 0, coarsest = 0;
+    int half = 1;
     for (int c = 0; c < (int)ctx->slots.size(); ++c) {
         const Slot& s = ctx->slots[c];
         if (!s.defined) continue;
         act.push_back(c);
+        if (s.hd.P.dts != 0.5) half = 0;
         int slot = 0;
         for (int y = 0; y < s.hd.P.ny; y += TY)
             for (int x = 0; x < s.hd.P.nx; x += TX) st.push_back(TileRef{c, x, y, slot++});
@@ -278,6 +295,7 @@ lbfs_status rebuild(lbfs_ctx* ctx) {
     ctx->n_pot = (int)pot.size();
     ctx->max_depth = depth;
     ctx->coarsest_cells = coarsest;
+    ctx->half = half;
     ctx->dirty = false;
     return LBFS_OK;
 }
@@ -343,8 +361,8 @@ lbfs_status one_step(lbfs_ctx* ctx) {
     toc(ctx, LBFS_TIMING_POTENTIAL, t0);
     for (int k = 0; k < 3; ++k) {
         cudaEvent_t t1 = tic(ctx);
-        LK(launch_stage(ctx->prec, ctx->cfg.tile, ctx->d_cases, ctx->d_stage_tiles, ctx->n_stage_tiles, k,
-                        ctx->stream));
+        LK(launch_stage(ctx->prec, ctx->cfg.tile, ctx->half, ctx->d_cases, ctx->d_stage_tiles,
+                        ctx->n_stage_tiles, k, ctx->stream));
         toc(ctx, LBFS_TIMING_STAGE, t1);
     }
     cudaEvent_t t2 = tic(ctx);
@@ -440,6 +458,8 @@ lbfs_status lbfs_set_case(lbfs_ctx* ctx, int32_t id, const lbfs_case_desc* desc)
         return fail(ctx, LBFS_EINVAL,
                     "grid sizes do not coarsen to <= 4096 cells by halving (use sizes with more factors of 2)");
     hd.nlev = nlev;
+    fill_phys<float>(P, hd.qf);
+    fill_phys<double>(P, hd.qd);
     const int TX = stage_tw(ctx), TY = stage_th(ctx);
     hd.red_tiles = ((P.nx + TX - 1) / TX) * ((P.ny + TY - 1) / TY);
     hd.mg_tiles = ((P.nx + kMgTX - 1) / kMgTX) * ((P.ny + kMgTY - 1) / kMgTY);
@@ -462,6 +482,7 @@ lbfs_status lbfs_set_case(lbfs_ctx* ctx, int32_t id, const lbfs_case_desc* desc)
     add((void**)&hd.phi64, cells * sizeof(double));
     if (ctx->prec != 0) add(&hd.phi, cells * rs);
     add(&hd.Fs_prev, cells * rs);
+    add(&hd.Sdot, cells * rs);
     for (int L = 0; L < nlev; ++L) {
         hd.lev[L].pitch = (int)align_up((size_t)hd.lev[L].nx, 32);
         const size_t lc = (size_t)hd.lev[L].pitch * hd.lev[L].ny;

@@ -32,6 +32,16 @@ struct CaseParams {
     double dt, dts, cp_ref, vol_ratio, H0, cos_t, sin_t;
 };
 
+// The per-point coefficients in the working precision R, converted once on the host
+// so that no kernel converts FP64 parameters inside its inner loops.
+template <class R>
+struct PhysT {
+    R rho_s, rho_l, rho_g, mu_s, mu_l, mu_g, lam_s, lam_l, lam_g;
+    R cp_s, cp_l, cp_g, chi_s, chi_l, chi_g;
+    R beta, kappa, Q_g, cp_ref, dts, inv_dts, inv_cpref_dts, tau_g, dt, vol_ratio, gravity, T_m, L;
+    R wall_T[4];
+};
+
 struct MGLevel {
     int nx, ny, pitch;
     void* mu;   // cell coefficient mu_m (M precision)
@@ -50,7 +60,10 @@ struct DevCase {
     void* C[3];
     void* phi;        // R copy of the potential read by the stage kernel
     double* phi64;    // FP64 master potential (== phi in FP64 mode)
-    void* Fs_prev;    // R
+    void* Fs_prev;    // R: F_s of the previous step, replaced by F_s^n in stage 1
+    void* Sdot;       // R: lagged dF_s/dt of the current step, written by stage 1
+    PhysT<float> qf;
+    PhysT<double> qd;
     int nlev;
     MGLevel lev[kMaxLevels];
     double* red;      // stage-tile partial sums, kRedN per tile
@@ -106,6 +119,42 @@ __device__ __forceinline__ void invert_enthalpy(const CaseParams& P, HR He, R C,
         T = R(P.T_m) + R(He - Hel) / cpL;
     }
 }
+
+template <class R>
+__device__ __forceinline__ R mix(R Fs, R C, R gs, R gl, R gg) {
+    const R liq = gg + C * (gl - gg);
+    return liq + Fs * (gs - liq);
+}
+
+// Eq. 8 as above with the two threshold differences H_e - H_es and H_e - H_el formed
+// in the enthalpy's precision H (FP64 storage in both modes) and everything after
+// them in R.  Hes_h = C_p,s T_m and L_h = L are given in H.
+template <class R, class H>
+__device__ __forceinline__ void invert_h(const PhysT<R>& Q, H Hes_h, H L_h, H He, R C, R& T, R& Fl) {
+    const R cpL = Q.cp_g + C * (Q.cp_l - Q.cp_g);
+    const H Hel = Q.T_m == R(0) ? L_h : L_h + H(cpL * Q.T_m);
+    const R ds = R(He - Hes_h), dl = R(He - Hel);
+    if (C < R(0.5)) {
+        Fl = R(1);
+        T = Q.T_m + dl / cpL;
+    } else if (ds < R(0)) {
+        Fl = R(0);
+        T = Q.T_m + ds / Q.cp_s;
+    } else if (dl <= R(0)) {
+        Fl = ds / (ds - dl);
+        T = Q.T_m;
+    } else {
+        Fl = R(1);
+        T = Q.T_m + dl / cpL;
+    }
+}
+
+template <class R>
+__device__ __forceinline__ const PhysT<R>& phys_of(const DevCase* dc);
+template <>
+__device__ __forceinline__ const PhysT<float>& phys_of<float>(const DevCase* dc) { return dc->qf; }
+template <>
+__device__ __forceinline__ const PhysT<double>& phys_of<double>(const DevCase* dc) { return dc->qd; }
 
 template <class R>
 __device__ __forceinline__ R load(const void* base, size_t idx) {

@@ -11,8 +11,10 @@ namespace lbfs {
 // stage kernel (lbfs_stage.cu); prec 0 = FP64, 1 = mixed
 int stage_tile_w(int prec, int tile);
 int stage_tile_h(int prec, int tile);
-cudaError_t launch_stage(int prec, int tile, const DevCase* cases, const TileRef* tiles, int ntiles,
-                         int stage, cudaStream_t st);
+// half: every case streams half a cell (dts = 1/2), which selects the reconstruction
+// without normal slopes at the upwind points
+cudaError_t launch_stage(int prec, int tile, int half, const DevCase* cases, const TileRef* tiles,
+                         int ntiles, int stage, cudaStream_t st);
 
 // potential multigrid (lbfs_potential.cu).  MG tiles are 32 x 8 cells of one level.
 constexpr int kMgTX = 32, kMgTY = 8;

@@ -3,9 +3,9 @@
 // cell quantities (Eq. 8 inversion, Eq. 11 mixture, velocity, mu_c, |H|^2), build
 // every face flux of the tile by the LBFS reconstruction (Eqs. 44, 45, 20, 28, 29,
 // 22, 32, 33, 43), add the sources (Eq. 41), form R(W) (Eq. 42) and the SSP-RK3
-// combination, and write the next stage.  The last stage also applies the step-end
-// rest condition of the solid, stores F_s^n for the next step's dF_s/dt, writes the
-// potential coefficient mu_m for the next solve, and reduces the diagnostics.
+// combination, and write the next stage.  Stage 1 also forms the lagged dF_s/dt of
+// the step; the last stage applies the step-end rest condition of the solid, writes
+// the potential coefficient mu_m for the next solve, and reduces the diagnostics.
 #include <cstdio>
 
 #include "lbfs_internal.cuh"
@@ -23,31 +23,47 @@ struct Geom {
 };
 
 // Per-face flux by the LBFS reconstruction, in the face frame (n normal, t
-// tangential).  Cells A (lower/left) and B (upper/right) at region indices kA, kB;
-// sn and st are the region strides along n and t.  Uses, for X = h, g and the
-// f^{eq-m} form of f, X*_a = (3/2 - tau) X_eq,a(x_f) + (tau - 1/2) X_eq,a(x - e_a dts),
-// which is Eqs. 16, 22, 32, 33 with X_neq = -tau (X_eq(x_f) - X_eq(x - e_a dts)),
-// and the D2Q9 moment identities for the interface equilibria.
-template <class R>
-__device__ __forceinline__ void face_flux(const CaseParams& P, const R* __restrict__ s, int RN,
-                                          int kA, int kB, int sn, int st, bool xface,
-                                          R& Fh, R& Fp, R& Fmn, R& Fmt, R& Fc) {
+// tangential).  Cells A (lower/left) and B (upper/right) at region indices kA and
+// kB = kA + sn; st is the region stride along t.  For X = h, g and the f^{eq-m} form
+// of f the starred distribution is X*_a = (3/2 - tau) X_eq,a(x_f) + (tau - 1/2)
+// X_eq,a(x - e_a dts) (Eqs. 16, 22, 32, 33 with X_neq = -tau (X_eq(x_f) -
+// X_eq(x - e_a dts))); the x_f parts of the fluxes follow from the D2Q9 moments of
+// the interface equilibria, so only the surrounding-point equilibria are summed per
+// direction.  HALF: the streaming step is half a cell, so the points of the
+// upwind cells sit on its centre line and the normal slopes drop out there.
+template <class R, bool HALF>
+__device__ __forceinline__ void face_flux(const PhysT<R>& Q, const R* __restrict__ s, int RN, int kA,
+                                          int sn, int st, bool xface, R& Fh, R& Fp, R& Fmn, R& Fmt,
+                                          R& Fc) {
+    const int kB = kA + sn;
     const int fun = xface ? SU : SV, fut = xface ? SV : SU;
     const int qf[7] = {SP, fun, fut, SC, SMU, ST, SHE};
-    R vA[7], nA[7], tA[7], vB[7], nB[7], tB[7];
+    const R dts = Q.dts;
+    // per primitive: A and B values, their tangential half-slopes, the mean of the two
+    // reconstructions at the face centre and half the mean tangential slope
+    R vA[7], hA[7], vB[7], hB[7], m0[7], hs[7], nA[7], nB[7];
 #pragma unroll
     for (int q = 0; q < 7; ++q) {
         const R* f = s + qf[q] * RN;
-        vA[q] = f[kA];
-        nA[q] = R(0.5) * (f[kA + sn] - f[kA - sn]);
-        tA[q] = R(0.5) * (f[kA + st] - f[kA - st]);
-        vB[q] = f[kB];
-        nB[q] = R(0.5) * (f[kB + sn] - f[kB - sn]);
-        tB[q] = R(0.5) * (f[kB + st] - f[kB - st]);
+        const R a = f[kA], b = f[kB];
+        const R na = R(0.5) * (b - f[kA - sn]);
+        const R nb = R(0.5) * (f[kB + sn] - a);
+        const R ta = R(0.5) * (f[kA + st] - f[kA - st]);
+        const R tb = R(0.5) * (f[kB + st] - f[kB - st]);
+        vA[q] = a;
+        vB[q] = b;
+        hA[q] = dts * ta;
+        hB[q] = dts * tb;
+        m0[q] = R(0.5) * (a + b) + R(0.25) * (na - nb);
+        hs[q] = R(0.5) * dts * (ta + tb);
+        if (!HALF) {
+            nA[q] = na;
+            nB[q] = nb;
+        }
     }
-    const R FsA = s[SFS * RN + kA], FsB = s[SFS * RN + kB];
-    const R dts = R(P.dts);
-    const R cpref = R(P.cp_ref), Qg = R(P.Q_g);
+    const R FsA = s[SFS * RN + kA], FsB = s[SFS * RN + kB], Fsm = R(0.5) * (FsA + FsB);
+    const R cpref = Q.cp_ref, Qg = Q.Q_g;
+    const R rs = Q.rho_s, rl = Q.rho_l, rg = Q.rho_g, cs = Q.cp_s, cl = Q.cp_l, cg = Q.cp_g;
     R Sp = 0, Sjn = 0, Sjt = 0, SC_ = 0, SH = 0, Ah = 0, Ag = 0;
     R Bpn = 0, Bpt = 0, BGn = 0, BGt = 0;
 #pragma unroll
@@ -56,30 +72,33 @@ __device__ __forceinline__ void face_flux(const CaseParams& P, const R* __restri
         const R w = R(d2q9_w(a));
         R q[7];
         R Fs;
-        const R ot = -R(et) * dts;
         if (en > 0) {
             const R on = R(0.5) - dts;
 #pragma unroll
-            for (int k = 0; k < 7; ++k) q[k] = vA[k] + on * nA[k] + ot * tA[k];
+            for (int k = 0; k < 7; ++k) {
+                q[k] = et == 0 ? vA[k] : (et > 0 ? vA[k] - hA[k] : vA[k] + hA[k]);
+                if (!HALF) q[k] += on * nA[k];
+            }
             Fs = FsA;
         } else if (en < 0) {
             const R on = R(-0.5) + dts;
 #pragma unroll
-            for (int k = 0; k < 7; ++k) q[k] = vB[k] + on * nB[k] + ot * tB[k];
+            for (int k = 0; k < 7; ++k) {
+                q[k] = et == 0 ? vB[k] : (et > 0 ? vB[k] - hB[k] : vB[k] + hB[k]);
+                if (!HALF) q[k] += on * nB[k];
+            }
             Fs = FsB;
         } else {
 #pragma unroll
-            for (int k = 0; k < 7; ++k)
-                q[k] = R(0.5) * ((vA[k] + R(0.5) * nA[k] + ot * tA[k]) +
-                                 (vB[k] - R(0.5) * nB[k] + ot * tB[k]));
-            Fs = R(0.5) * (FsA + FsB);
+            for (int k = 0; k < 7; ++k) q[k] = et == 0 ? m0[k] : (et > 0 ? m0[k] - hs[k] : m0[k] + hs[k]);
+            Fs = Fsm;
         }
         const R p = q[0], un = q[1], ut = q[2], C = q[3], mu = q[4], T = q[5], He = q[6];
-        const R rho = mixture(Fs, C, P.rho_s, P.rho_l, P.rho_g);
-        const R cp = mixture(Fs, C, P.cp_s, P.cp_l, P.cp_g);
+        const R rho = mix(Fs, C, rs, rl, rg);
+        const R cp = mix(Fs, C, cs, cl, cg);
         const R eu = R(en) * un + R(et) * ut;
         const R uu = un * un + ut * ut;
-        const R G = R(3) * eu + R(4.5) * eu * eu - R(1.5) * uu;   // Gamma_a(u)
+        const R G = eu * (R(3) + R(4.5) * eu) - R(1.5) * uu;   // Gamma_a(u)
         const R feq = w * (p + rho * G * R(1.0 / 3.0));
         R geq, heq;
         if (a == 0) {
@@ -87,11 +106,11 @@ __device__ __forceinline__ void face_flux(const CaseParams& P, const R* __restri
             heq = He - cpref * T + w * (cpref * T - R(1.5) * cp * T * uu);
         } else {
             geq = R(3) * w * (mu * Qg + C * eu);
-            heq = w * (cpref * T + cp * T * G);
+            heq = w * T * (cpref + cp * G);
         }
         Sp += feq;
-        Sjn += R(en) * feq;
-        Sjt += R(et) * feq;
+        if (en != 0) Sjn += R(en) * feq;
+        if (et != 0) Sjt += R(et) * feq;
         SC_ += geq;
         SH += heq;
         if (en != 0) {
@@ -106,19 +125,18 @@ __device__ __forceinline__ void face_flux(const CaseParams& P, const R* __restri
         }
     }
     // Eq. 45: interface values
-    const R Fsf = R(0.5) * (FsA + FsB);
     const R Cf = SC_, pf = Sp, Hef = SH;
-    const R rhof = mixture(Fsf, Cf, P.rho_s, P.rho_l, P.rho_g);
+    const R rhof = mix(Fsm, Cf, rs, rl, rg);
     const R inv_rc = R(3) / rhof;                 // 1 / (rho_f c_s^2)
     const R ufn = Sjn * inv_rc, uft = Sjt * inv_rc;
-    const R cpf = mixture(Fsf, Cf, P.cp_s, P.cp_l, P.cp_g);
-    const R lamf = mixture(Fsf, Cf, P.lam_s, P.lam_l, P.lam_g);
-    const R muf = mixture(Fsf, Cf, P.mu_s, P.mu_l, P.mu_g);
+    const R cpf = mix(Fsm, Cf, cs, cl, cg);
+    const R lamf = mix(Fsm, Cf, Q.lam_s, Q.lam_l, Q.lam_g);
+    const R muf = mix(Fsm, Cf, Q.mu_s, Q.mu_l, Q.mu_g);
     R Tf, Flf;
-    invert_enthalpy<R, R>(P, Hef, Cf, Tf, Flf);
-    const R tau_f = R(0.5) + muf * inv_rc / dts;
-    const R tau_h = R(0.5) + lamf * inv_rc / (cpref * dts);
-    const R tau_g = R(0.5) + R(P.mobility) / (Qg * dts);
+    invert_h<R, R>(Q, cs * Q.T_m, Q.L, Hef, Cf, Tf, Flf);
+    const R tau_f = R(0.5) + muf * inv_rc * Q.inv_dts;
+    const R tau_h = R(0.5) + lamf * inv_rc * Q.inv_cpref_dts;
+    const R tau_g = Q.tau_g;
     const R c3 = R(1.0 / 3.0);
     Fh = (R(1.5) - tau_h) * cpf * Tf * ufn + (tau_h - R(0.5)) * Ah;
     Fc = (R(1.5) - tau_g) * Cf * ufn + (tau_g - R(0.5)) * Ag;
@@ -131,16 +149,16 @@ __device__ __forceinline__ void face_flux(const CaseParams& P, const R* __restri
 // half a cell from the inner centre; enthalpy flux -(lambda/rho) dT/dn on Dirichlet
 // walls, zero on adiabatic ones; no mass or phase-field flux.
 template <class R>
-__device__ __forceinline__ void wall_flux(const CaseParams& P, const R* __restrict__ s, int RN,
-                                          int k, int wall, R F[5]) {
+__device__ __forceinline__ void wall_flux(const PhysT<R>& Q, int dirichlet, const R* __restrict__ s,
+                                          int RN, int k, int wall, R F[5]) {
     const R Fs = s[SFS * RN + k], C = s[SC * RN + k];
     const R rho = s[SRHO * RN + k];
-    const R mu = mixture(Fs, C, P.mu_s, P.mu_l, P.mu_g);
-    const R lam = mixture(Fs, C, P.lam_s, P.lam_l, P.lam_g);
+    const R mu = mix(Fs, C, Q.mu_s, Q.mu_l, Q.mu_g);
+    const R lam = mix(Fs, C, Q.lam_s, Q.lam_l, Q.lam_g);
     const R side = (wall == 0 || wall == 2) ? R(1) : R(-1);
     const R ut = wall < 2 ? s[SV * RN + k] : s[SU * RN + k];
     const R dut = side * ut * R(2);
-    const R dT = side * (s[ST * RN + k] - R(P.wall_T[wall])) * R(2);
+    const R dT = side * (s[ST * RN + k] - Q.wall_T[wall]) * R(2);
     const R c3 = R(1.0 / 3.0);
     F[1] = R(0);
     F[4] = R(0);
@@ -151,19 +169,20 @@ __device__ __forceinline__ void wall_flux(const CaseParams& P, const R* __restri
         F[3] = c3 * s[SP * RN + k];
         F[2] = c3 * (-mu * dut);
     }
-    F[0] = P.thermal_dir[wall] ? -(lam / rho) * dT : R(0);
+    F[0] = dirichlet ? -(lam / rho) * dT : R(0);
 }
 
-template <class R, class HR, int TX, int TY, int NT>
-__global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ cases,
-                                                   const TileRef* __restrict__ tiles, int stage) {
+template <class R, class HR, int TX, int TY, int NT, int MINB, bool HALF>
+__global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restrict__ cases,
+                                                         const TileRef* __restrict__ tiles, int stage) {
     using Gm = Geom<TX, TY>;
     constexpr int RW = Gm::RW, RH = Gm::RH, RN = Gm::RN, NFX = Gm::NFX, NF = Gm::NF;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     R* s = reinterpret_cast<R*>(smem_raw);
-    R* flux = s + NSH * RN;                                         // [5][NF]
+    R* flux = s + NSH * RN;                                             // [5][NF]
     signed char* kind = reinterpret_cast<signed char*>(flux + 5 * NF);  // [RN]
     __shared__ CaseParams P;
+    __shared__ PhysT<R> Q;
     __shared__ double red_s[32][kRedN];
 
     const TileRef tr = tiles[blockIdx.x];
@@ -172,6 +191,9 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
         const int* src = reinterpret_cast<const int*>(&dc->P);
         int* dst = reinterpret_cast<int*>(&P);
         for (int i = threadIdx.x; i < (int)(sizeof(CaseParams) / sizeof(int)); i += NT) dst[i] = src[i];
+        const int* srq = reinterpret_cast<const int*>(&phys_of<R>(dc));
+        int* dsq = reinterpret_cast<int*>(&Q);
+        for (int i = threadIdx.x; i < (int)(sizeof(PhysT<R>) / sizeof(int)); i += NT) dsq[i] = srq[i];
     }
     const int in = stage == 0 ? 0 : (stage == 1 ? 1 : 2);
     const int out = stage == 0 ? 1 : (stage == 1 ? 2 : 0);
@@ -184,6 +206,7 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
     __syncthreads();
     const int nx = P.nx, ny = P.ny, pitch = P.pitch;
     const int x0 = tr.x0, y0 = tr.y0;
+    const HR Hes_h = HR(P.cp_s) * HR(P.T_m), L_h = HR(P.L);
 
     // ---- phase 1: load the stage state with halo, ghost rules at walls ----------
     for (int k = threadIdx.x; k < RN; k += NT) {
@@ -191,7 +214,7 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
         const int gx = x0 - Gm::H + lx, gy = y0 - Gm::H + ly;
         int sx, sy, xs, ys;  // source cell and status: 0 inside, 1 ghost low, 2 ghost high, 3 far
         if (P.periodic_x) {
-            sx = ((gx % nx) + nx) % nx;
+            sx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
             xs = 0;
         } else if (gx >= 0 && gx < nx) {
             sx = gx; xs = 0;
@@ -203,7 +226,7 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
             sx = gx < 0 ? 0 : nx - 1; xs = 3;
         }
         if (P.periodic_y) {
-            sy = ((gy % ny) + ny) % ny;
+            sy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
             ys = 0;
         } else if (gy >= 0 && gy < ny) {
             sy = gy; ys = 0;
@@ -214,6 +237,9 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
         } else {
             sy = gy < 0 ? 0 : ny - 1; ys = 3;
         }
+        // a periodic halo can reach past one period only on grids narrower than the halo
+        sx = sx < 0 ? 0 : (sx >= nx ? nx - 1 : sx);
+        sy = sy < 0 ? 0 : (sy >= ny ? ny - 1 : sy);
         int wall = -1;
         signed char kd;
         if (xs == 0 && ys == 0) {
@@ -231,18 +257,19 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
         const HR He = gHe[gi];
         const R C = gC[gi];
         R T, Fl;
-        invert_enthalpy<R, HR>(P, He, C, T, Fl);
+        invert_h<R, HR>(Q, Hes_h, L_h, He, C, T, Fl);
         const R Fs = R(1) - Fl;
-        const R rho = mixture(Fs, C, P.rho_s, P.rho_l, P.rho_g);
-        R u = gMx[gi] * R(3) / rho, v = gMy[gi] * R(3) / rho;
+        const R rho = mix(Fs, C, Q.rho_s, Q.rho_l, Q.rho_g);
+        const R rinv = R(3) / rho;
+        R u = gMx[gi] * rinv, v = gMy[gi] * rinv;
         R phi = gPhi[gi];
         R Hes = R(He);
         if (wall >= 0) {
             u = -u;
             v = -v;
-            if (P.thermal_dir[wall]) T = R(2) * R(P.wall_T[wall]) - T;
-            const R cp = mixture(Fs, C, P.cp_s, P.cp_l, P.cp_g);
-            Hes = cp * T + R(P.L) * (R(1) - Fs);
+            if (P.thermal_dir[wall]) T = R(2) * Q.wall_T[wall] - T;
+            const R cp = mix(Fs, C, Q.cp_s, Q.cp_l, Q.cp_g);
+            Hes = cp * T + Q.L * (R(1) - Fs);
             if (P.mag_dir[wall]) {
                 double wx = wall == 0 ? 0.0 : (wall == 1 ? (double)nx : sx + 0.5);
                 double wy = wall == 2 ? 0.0 : (wall == 3 ? (double)ny : sy + 0.5);
@@ -263,15 +290,14 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
     }
     __syncthreads();
     // ---- phase 2: mu_c and |H|^2 at inner cells -------------------------------
-    const R beta = R(P.beta), kappa = R(P.kappa);
     for (int k = threadIdx.x; k < RN; k += NT) {
         const int lx = k % RW, ly = k / RW;
         R mu = 0, h2 = 0;
         if (kind[k] == 0 && lx > 0 && lx < RW - 1 && ly > 0 && ly < RH - 1) {
             const R* c = s + SC * RN;
             const R C = c[k];
-            const R lap = c[k + 1] + c[k - 1] + c[k + RW] + c[k - RW] - R(4) * C;
-            mu = R(2) * beta * C * (C - R(1)) * (R(2) * C - R(1)) - kappa * lap;
+            const R lap = (c[k + 1] + c[k - 1]) + (c[k + RW] + c[k - RW]) - R(4) * C;
+            mu = R(2) * Q.beta * C * (C - R(1)) * (R(2) * C - R(1)) - Q.kappa * lap;
             const R* ph = s + SPHI * RN;
             const R hx = R(-0.5) * (ph[k + 1] - ph[k - 1]);
             const R hy = R(-0.5) * (ph[k + RW] - ph[k - RW]);
@@ -284,11 +310,10 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
     for (int k = threadIdx.x; k < RN; k += NT) {
         const int kd = kind[k];
         if (kd >= 1 && kd <= 4) {
-            const int lx = k % RW, ly = k / RW;
             const int w = kd - 1;
-            int ks = k + (w == 0 ? 1 : w == 1 ? -1 : w == 2 ? RW : -RW);
+            const int ks = k + (w == 0 ? 1 : w == 1 ? -1 : w == 2 ? RW : -RW);
             const int sx = ks % RW, sy = ks / RW;
-            if (sx > 0 && sx < RW - 1 && sy > 0 && sy < RH - 1 && lx >= 0 && ly >= 0) {
+            if (sx > 0 && sx < RW - 1 && sy > 0 && sy < RH - 1) {
                 s[SMU * RN + k] = s[SMU * RN + ks];
                 s[SH2 * RN + k] = s[SH2 * RN + ks];
             }
@@ -304,11 +329,11 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
             if (gy < ny && gxf <= nx) {
                 const int kB = (ty + Gm::H) * RW + fx + Gm::H, kA = kB - 1;
                 if (!P.periodic_x && gxf == 0) {
-                    wall_flux<R>(P, s, RN, kB, 0, F);
+                    wall_flux<R>(Q, P.thermal_dir[0], s, RN, kB, 0, F);
                 } else if (!P.periodic_x && gxf == nx) {
-                    wall_flux<R>(P, s, RN, kA, 1, F);
+                    wall_flux<R>(Q, P.thermal_dir[1], s, RN, kA, 1, F);
                 } else {
-                    face_flux<R>(P, s, RN, kA, kB, 1, RW, true, F[0], F[1], F[2], F[3], F[4]);
+                    face_flux<R, HALF>(Q, s, RN, kA, 1, RW, true, F[0], F[1], F[2], F[3], F[4]);
                 }
             }
         } else {
@@ -318,11 +343,11 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
             if (gx < nx && gyf <= ny) {
                 const int kB = (fy + Gm::H) * RW + tx + Gm::H, kA = kB - RW;
                 if (!P.periodic_y && gyf == 0) {
-                    wall_flux<R>(P, s, RN, kB, 2, F);
+                    wall_flux<R>(Q, P.thermal_dir[2], s, RN, kB, 2, F);
                 } else if (!P.periodic_y && gyf == ny) {
-                    wall_flux<R>(P, s, RN, kA, 3, F);
+                    wall_flux<R>(Q, P.thermal_dir[3], s, RN, kA, 3, F);
                 } else {
-                    face_flux<R>(P, s, RN, kA, kB, RW, 1, false, F[0], F[1], F[3], F[2], F[4]);
+                    face_flux<R, HALF>(Q, s, RN, kA, RW, 1, false, F[0], F[1], F[3], F[2], F[4]);
                 }
             }
         }
@@ -334,7 +359,7 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
     const R c3 = R(1.0 / 3.0);
     const double a_rk = stage == 0 ? 0.0 : (stage == 1 ? 0.75 : 1.0 / 3.0);
     const double b_rk = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
-    const R dt = R(P.dt);
+    const R dt = Q.dt;
     double acc[kRedN] = {0, 0, 0, 0, 0, 0};
     HR* oHe = static_cast<HR*>(dc->He[out]);
     R* oP = static_cast<R*>(dc->p[out]);
@@ -347,6 +372,7 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
     const R* bMy = static_cast<const R*>(dc->my[0]);
     const R* bC = static_cast<const R*>(dc->C[0]);
     R* Fsp = static_cast<R*>(dc->Fs_prev);
+    R* Sdp = static_cast<R*>(dc->Sdot);
     for (int c = threadIdx.x; c < TX * TY; c += NT) {
         const int tx = c % TX, ty = c / TX;
         const int gx = x0 + tx, gy = y0 + ty;
@@ -360,8 +386,8 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
                     (flux[q * NF + fb + TX] - flux[q * NF + fb]);
         const R Fs = s[SFS * RN + k], C = s[SC * RN + k], T = s[ST * RN + k];
         const R u = s[SU * RN + k], v = s[SV * RN + k], rho = s[SRHO * RN + k];
-        const R cp = mixture(Fs, C, P.cp_s, P.cp_l, P.cp_g);
-        const R chi = mixture(Fs, C, P.chi_s, P.chi_l, P.chi_g);
+        const R cp = mix(Fs, C, Q.cp_s, Q.cp_l, Q.cp_g);
+        const R chi = mix(Fs, C, Q.chi_s, Q.chi_l, Q.chi_g);
         const R divu = R(0.5) * (s[SU * RN + k + 1] - s[SU * RN + k - 1]) +
                        R(0.5) * (s[SV * RN + k + RW] - s[SV * RN + k - RW]);
         const R drx = R(0.5) * (s[SRHO * RN + k + 1] - s[SRHO * RN + k - 1]);
@@ -371,24 +397,25 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
         const R dmx = R(0.5) * (s[SMU * RN + k + 1] - s[SMU * RN + k - 1]);
         const R dmy = R(0.5) * (s[SMU * RN + k + RW] - s[SMU * RN + k - RW]);
         const size_t gi = (size_t)gy * pitch + gx;
-        // W^n at this cell and the lagged dF_s/dt
-        const HR He0 = bHe[gi];
-        const R C0 = bC[gi];
-        R T0, Fl0;
-        invert_enthalpy<R, HR>(P, He0, C0, T0, Fl0);
-        const R Fs_n = R(1) - Fl0;
-        const R Sd = (Fs_n - Fsp[gi]) / dt;
-        const R vr = R(P.vol_ratio);
+        // lagged dF_s/dt: formed by stage 1 from F_s^n (this stage's own input) and the
+        // previous step's F_s, which is then replaced by F_s^n
+        R Sd;
+        if (stage == 0) {
+            Sd = (Fs - Fsp[gi]) / dt;
+            Fsp[gi] = Fs;
+            Sdp[gi] = Sd;
+        } else {
+            Sd = Sdp[gi];
+        }
+        const R vr = Q.vol_ratio;
         Rw[0] += cp * T * divu;
-        Rw[1] += u * c3 * drx + v * c3 * dry + rho * c3 * vr * Sd;
+        Rw[1] += c3 * (u * drx + v * dry) + rho * c3 * vr * Sd;
         Rw[2] += c3 * (-C * dmx + R(0.5) * chi * dhx - rho * u * Sd);
-        Rw[3] += c3 * (-C * dmy + R(0.5) * chi * dhy + rho * R(P.gravity) - rho * v * Sd);
+        Rw[3] += c3 * (-C * dmy + R(0.5) * chi * dhy + rho * Q.gravity - rho * v * Sd);
         Rw[4] += C * vr * Sd;
         // stage input at this cell
         const HR Hek = gHe[gi];
         const R pk = gP[gi], mxk = gMx[gi], myk = gMy[gi], Ck = gC[gi];
-        const HR aH = HR(a_rk), bH = HR(b_rk);
-        const R a = R(a_rk), b = R(b_rk);
         HR Hen;
         R pn, mxn, myn, Cn;
         if (stage == 0) {
@@ -398,22 +425,23 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
             myn = myk + dt * Rw[3];
             Cn = Ck + dt * Rw[4];
         } else {
-            Hen = aH * He0 + bH * (Hek + HR(dt) * HR(Rw[0]));
+            const HR aH = HR(a_rk), bH = HR(b_rk);
+            const R a = R(a_rk), b = R(b_rk);
+            Hen = aH * bHe[gi] + bH * (Hek + HR(dt) * HR(Rw[0]));
             pn = a * bP[gi] + b * (pk + dt * Rw[1]);
             mxn = a * bMx[gi] + b * (mxk + dt * Rw[2]);
             myn = a * bMy[gi] + b * (myk + dt * Rw[3]);
-            Cn = a * C0 + b * (Ck + dt * Rw[4]);
+            Cn = a * bC[gi] + b * (Ck + dt * Rw[4]);
         }
         if (stage == 2) {
             // step end: solid held at rest, (rho u) <- (1 - F_s)(rho u)
             R Tn, Fln;
-            invert_enthalpy<R, HR>(P, Hen, Cn, Tn, Fln);
+            invert_h<R, HR>(Q, Hes_h, L_h, Hen, Cn, Tn, Fln);
             mxn *= Fln;
             myn *= Fln;
-            Fsp[gi] = Fs_n;
             const R Fsn = R(1) - Fln;
             R* mu0 = static_cast<R*>(dc->lev[0].mu);
-            mu0[(size_t)gy * dc->lev[0].pitch + gx] = R(1) + mixture(Fsn, Cn, P.chi_s, P.chi_l, P.chi_g);
+            mu0[(size_t)gy * dc->lev[0].pitch + gx] = R(1) + mix(Fsn, Cn, Q.chi_s, Q.chi_l, Q.chi_g);
             acc[0] += (double)Cn;
             acc[1] += (double)Hen;
             if (Cn >= R(0.5)) {
@@ -421,8 +449,8 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
                 acc[3] += 1.0;
                 acc[4] += (double)Fsn;
             }
-            const bool fin = isfinite((double)Hen) && isfinite((double)pn) && isfinite((double)mxn) &&
-                             isfinite((double)myn) && isfinite((double)Cn);
+            const bool fin = isfinite((double)Hen) && isfinite(pn) && isfinite(mxn) && isfinite(myn) &&
+                             isfinite(Cn);
             if (!fin) acc[5] += 1.0;
         }
         oHe[gi] = Hen;
@@ -450,28 +478,32 @@ __global__ void __launch_bounds__(NT) stage_kernel(const DevCase* __restrict__ c
 }
 
 // ---- launch helpers ------------------------------------------------------------
-template <class R, class HR, int TX, int TY>
-struct StageCfg {
+template <int TX, int TY>
+struct StageShape {
     static constexpr int NT = ((2 * TX * TY + TX + TY) / 2 + 31) / 32 * 32;
+    template <class R>
     static constexpr size_t smem() {
         using Gm = Geom<TX, TY>;
         return (size_t)(NSH * Gm::RN + 5 * Gm::NF) * sizeof(R) + Gm::RN + 16;
     }
 };
 
-template <class R, class HR, int TX, int TY>
-static cudaError_t launch_stage_t(const DevCase* cases, const TileRef* tiles, int ntiles, int stage,
-                                  cudaStream_t st) {
-    using Cf = StageCfg<R, HR, TX, TY>;
-    auto kern = stage_kernel<R, HR, TX, TY, Cf::NT>;
+template <class R, class HR, int TX, int TY, int MINB, bool HALF>
+static cudaError_t launch_t(const DevCase* cases, const TileRef* tiles, int ntiles, int stage,
+                            cudaStream_t st) {
+    using S = StageShape<TX, TY>;
+    auto kern = stage_kernel<R, HR, TX, TY, S::NT, MINB, HALF>;
     static bool attr_set = false;
+    const size_t sm = S::template smem<R>();
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)Cf::smem());
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        if (e != cudaSuccess) return e;
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    kern<<<ntiles, Cf::NT, Cf::smem(), st>>>(cases, tiles, stage);
+    kern<<<ntiles, S::NT, sm, st>>>(cases, tiles, stage);
     return cudaGetLastError();
 }
 
@@ -481,16 +513,21 @@ int stage_tile_w(int prec, int tile) {
     return 32;
 }
 int stage_tile_h(int prec, int tile) {
+    (void)prec;
     (void)tile;
-    return prec == 0 ? 8 : 8;
+    return 8;
 }
 
-cudaError_t launch_stage(int prec, int tile, const DevCase* cases, const TileRef* tiles, int ntiles,
-                         int stage, cudaStream_t st) {
+cudaError_t launch_stage(int prec, int tile, int half, const DevCase* cases, const TileRef* tiles,
+                         int ntiles, int stage, cudaStream_t st) {
     (void)tile;
     if (ntiles <= 0) return cudaSuccess;
-    if (prec == 0) return launch_stage_t<double, double, 32, 8>(cases, tiles, ntiles, stage, st);
-    return launch_stage_t<float, double, 32, 8>(cases, tiles, ntiles, stage, st);
+    if (prec == 0) {
+        if (half) return launch_t<double, double, 32, 8, 1, true>(cases, tiles, ntiles, stage, st);
+        return launch_t<double, double, 32, 8, 1, false>(cases, tiles, ntiles, stage, st);
+    }
+    if (half) return launch_t<float, double, 32, 8, 2, true>(cases, tiles, ntiles, stage, st);
+    return launch_t<float, double, 32, 8, 2, false>(cases, tiles, ntiles, stage, st);
 }
 
 }  // namespace lbfs
