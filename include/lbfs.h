@@ -60,7 +60,10 @@ typedef struct lbfs_config {
     void*   alloc_user;
     int32_t mg_max_cycles;   /* potential refinement cycles per step (0: 40)                 */
     double  mg_tol;          /* relative residual ||b - A phi|| / ||b|| (0: 1e-13 FP64,
-                                1e-8 mixed)                                                */
+                                1e-6 mixed).  FP64 steps and the first mixed step after a
+                                state is set iterate to it; later mixed steps run at most
+                                one refinement cycle, skipped on the device when the
+                                residual already meets it                                  */
     int32_t tile;            /* stage-kernel tile shape id (0: the tuned default)           */
     int32_t reserved[7];
 } lbfs_config;

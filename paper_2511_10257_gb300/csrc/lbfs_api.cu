@@ -60,8 +60,11 @@ struct lbfs_ctx {
     double mg_tol = 0.0;
     int mg_max_cycles = 0;
     int half = 0;          // every defined case has dts = 1/2
+    bool pot_fresh = true; // a state was set since the last full potential solve
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
+    int64_t graph_launches = 0;       // kernel nodes in one recorded step
+    cudaStream_t cap_stream = nullptr; // private stream used to record the graph
     // kernel timing (events on the context stream)
     bool timing = false;
     double t_ms[3] = {0, 0, 0};
@@ -330,16 +333,31 @@ lbfs_status vcycle(lbfs_ctx* ctx) {
     return LBFS_OK;
 }
 
+// The potential of the current state.  A full solve (host-checked refinement cycles
+// until every case meets mg_tol) runs in FP64 mode and, in mixed mode, after a
+// state was set.  A warm mixed step runs one refinement cycle with no host round
+// trip: the residual's norm sets a per-case flag on the device and the V-cycle and
+// correction kernels skip converged cases.
 lbfs_status potential_solve(lbfs_ctx* ctx) {
     if (ctx->n_pot == 0) return LBFS_OK;
     const int p = ctx->prec;
     cudaStream_t s = ctx->stream;
     for (int L = 1; L < ctx->max_depth; ++L)
         LK(launch_mg_restrict_mu(p, ctx->d_cases, ctx->d_mg_tiles[L], ctx->n_mg_tiles[L], L, s));
+    const double no_fail = 1e300;
+    if (p != 0 && !ctx->pot_fresh) {
+        LK(launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], s));
+        LK(launch_mg_finalize(ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, ctx->mg_tol * 1e4, 1,
+                              ctx->d_flag, s));
+        lbfs_status r = vcycle(ctx);
+        if (r != LBFS_OK) return r;
+        LK(launch_mg_correct(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], s));
+        return LBFS_OK;
+    }
     for (int it = 0;; ++it) {
         LK(launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], s));
         CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
-        LK(launch_mg_finalize(ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, it == 0, ctx->d_flag, s));
+        LK(launch_mg_finalize(ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, no_fail, it == 0, ctx->d_flag, s));
         CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (*ctx->h_flag == 0) break;
@@ -351,6 +369,7 @@ lbfs_status potential_solve(lbfs_ctx* ctx) {
         if (r != LBFS_OK) return r;
         LK(launch_mg_correct(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], s));
     }
+    ctx->pot_fresh = false;
     return LBFS_OK;
 }
 
@@ -368,6 +387,32 @@ lbfs_status one_step(lbfs_ctx* ctx) {
     cudaEvent_t t2 = tic(ctx);
     LK(launch_step_finalize(ctx->d_cases, ctx->d_active, ctx->n_active, ctx->stream));
     toc(ctx, LBFS_TIMING_FINALIZE, t2);
+    return LBFS_OK;
+}
+
+// Record one warm step as a CUDA graph on a private stream (capture is not allowed
+// on the legacy default stream a caller may lend us); replay it on ctx->stream.
+lbfs_status record_graph(lbfs_ctx* ctx) {
+    drop_graph(ctx);
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = ctx->stream;
+    const int64_t l0 = ctx->launches;
+    ctx->stream = ctx->cap_stream;
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+    lbfs_status r = e == cudaSuccess ? one_step(ctx) : LBFS_ECUDA;
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
+    ctx->stream = user;
+    ctx->graph_launches = ctx->launches - l0;
+    ctx->launches = l0;
+    if (e != cudaSuccess) return fail(ctx, LBFS_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    if (r != LBFS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+    }
+    if (e2 != cudaSuccess) return fail(ctx, LBFS_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e2));
+    ctx->graph = g;
+    CK(cudaGraphInstantiate(&ctx->gexec, g, 0));
     return LBFS_OK;
 }
 
@@ -402,7 +447,7 @@ lbfs_status lbfs_create(const lbfs_config* cfg, lbfs_ctx** out) {
     lbfs_ctx* ctx = new lbfs_ctx();
     ctx->cfg = *cfg;
     ctx->prec = cfg->precision;
-    ctx->mg_tol = cfg->mg_tol > 0 ? cfg->mg_tol : (ctx->prec == 0 ? 1e-13 : 1e-8);
+    ctx->mg_tol = cfg->mg_tol > 0 ? cfg->mg_tol : (ctx->prec == 0 ? 1e-13 : 1e-6);
     ctx->mg_max_cycles = cfg->mg_max_cycles > 0 ? cfg->mg_max_cycles : 40;
     ctx->slots.resize(cfg->max_cases);
     if (cfg->cuda_stream) {
@@ -522,6 +567,7 @@ lbfs_status lbfs_set_case(lbfs_ctx* ctx, int32_t id, const lbfs_case_desc* desc)
     CK(launch_stats_init(ctx->prec, dcase, P.nx, P.ny, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     s.defined = true;
+    ctx->pot_fresh = true;
     return LBFS_OK;
 }
 
@@ -552,6 +598,7 @@ lbfs_status lbfs_set_fields(lbfs_ctx* ctx, int32_t id, uint32_t mask, const doub
     CK(launch_mu_from_state(ctx->prec, dcase, s.hd.P.nx, s.hd.P.ny, ctx->stream));
     CK(launch_stats_init(ctx->prec, dcase, s.hd.P.nx, s.hd.P.ny, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
+    ctx->pot_fresh = true;
     return LBFS_OK;
 }
 
@@ -582,7 +629,22 @@ lbfs_status lbfs_step(lbfs_ctx* ctx, int32_t nsteps, lbfs_case_stats* out) {
     CK(cudaSetDevice(ctx->cfg.device));
     ctx->launches = 0;
     ctx->pot_fail = false;
+    for (size_t c = 0; c < ctx->slots.size(); ++c)
+        if (ctx->slots[c].defined)
+            CK(cudaMemsetAsync(ctx->d_stats + c * kStatN + ST_POT_FAIL, 0, sizeof(double), ctx->stream));
     for (int n = 0; n < nsteps && ctx->n_active > 0; ++n) {
+        // a warm mixed-precision step has no host round trip and can be replayed
+        const bool graphable = ctx->cfg.use_graph && !ctx->timing && (ctx->prec != 0 || ctx->n_pot == 0) &&
+                               !(ctx->n_pot > 0 && ctx->pot_fresh);
+        if (graphable) {
+            if (!ctx->gexec) {
+                lbfs_status r = record_graph(ctx);
+                if (r != LBFS_OK) return r;
+            }
+            CK(cudaGraphLaunch(ctx->gexec, ctx->stream));
+            ctx->launches += ctx->graph_launches;
+            continue;
+        }
         lbfs_status r = one_step(ctx);
         if (r != LBFS_OK) return r;
     }
@@ -594,6 +656,7 @@ lbfs_status lbfs_step(lbfs_ctx* ctx, int32_t nsteps, lbfs_case_stats* out) {
     for (size_t c = 0; c < ctx->slots.size(); ++c) {
         const double* st = ctx->h_stats + c * kStatN;
         if (ctx->slots[c].defined && st[ST_NONFINITE] > 0) bad = true;
+        if (ctx->slots[c].defined && st[ST_POT_FAIL] > 0) ctx->pot_fail = true;
         if (out) {
             lbfs_case_stats& o = out[c];
             std::memset(&o, 0, sizeof(o));
@@ -646,6 +709,7 @@ void lbfs_destroy(lbfs_ctx* ctx) {
     drop_graph(ctx);
     harvest(ctx);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (Slot& s : ctx->slots) free_slot(ctx, s);
     for (auto* p : ctx->d_mg_tiles) dfree(ctx, p);
     dfree(ctx, ctx->d_stage_tiles);

@@ -22,8 +22,9 @@ cudaError_t launch_mg_restrict_mu(int prec, const DevCase* cases, const TileRef*
                                   int level_coarse, cudaStream_t st);
 cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* tiles, int n,
                                  cudaStream_t st);
+// tol: the convergence test; a residual above fail_tol marks the case's solve failed
 cudaError_t launch_mg_finalize(const DevCase* cases, const int* case_ids, int ncases, double tol,
-                               int first, int* not_done, cudaStream_t st);
+                               double fail_tol, int first, int* not_done, cudaStream_t st);
 cudaError_t launch_mg_smooth(int prec, const DevCase* cases, const TileRef* tiles, int n, int level,
                              int color, cudaStream_t st);
 cudaError_t launch_mg_restrict_resid(int prec, const DevCase* cases, const TileRef* tiles, int n,

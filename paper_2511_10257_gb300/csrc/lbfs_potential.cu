@@ -103,24 +103,28 @@ __global__ void __launch_bounds__(kNT) k_residual64(const DevCase* __restrict__ 
         const M* mu = static_cast<const M*>(lv.mu);
         const double* ph = dc->phi64;
         const size_t k = (size_t)j * lv.pitch + i;
-        const double mc = (double)mu[k], pc = ph[k];
-        double diag = 0.0, off = 0.0, b = 0.0;
+        const M mcm = mu[k];
+        const double pc = ph[k];
+        // face coefficients in M (they are M-precision data), potentials and the
+        // accumulation of the residual in FP64
+        M diag = 0;
+        double off = 0.0, b = 0.0;
         for (int w = 0; w < 4; ++w) {
             int ii, jj;
             if (neighbour(P, lv.nx, lv.ny, i, j, w, ii, jj)) {
                 const size_t kn = (size_t)jj * lv.pitch + ii;
-                const double mf = 0.5 * (mc + (double)mu[kn]);
+                const M mf = M(0.5) * (mcm + mu[kn]);
                 diag += mf;
-                off += mf * ph[kn];
+                off += (double)mf * ph[kn];
             } else if (P.mag_dir[w]) {
                 const double wx = w == 0 ? 0.0 : (w == 1 ? (double)lv.nx : i + 0.5);
                 const double wy = w == 2 ? 0.0 : (w == 3 ? (double)lv.ny : j + 0.5);
                 const double pw = -P.H0 * (wx * P.cos_t + wy * P.sin_t);
-                diag += 2.0 * mc;
-                b += 2.0 * mc * pw;
+                diag += M(2) * mcm;
+                b += 2.0 * (double)mcm * pw;
             }
         }
-        const double r = b - (diag * pc - off);
+        const double r = b - ((double)diag * pc - off);
         static_cast<M*>(lv.r)[k] = M(r);
         static_cast<M*>(lv.e)[k] = M(0);
         r2 = r * r;
@@ -136,7 +140,7 @@ __global__ void __launch_bounds__(kNT) k_residual64(const DevCase* __restrict__ 
 
 // one block per case: relative residual, convergence flag, cycle count
 __global__ void k_mg_finalize(const DevCase* __restrict__ cases, const int* __restrict__ ids,
-                              double tol, int first, int* not_done) {
+                              double tol, double fail_tol, int first, int* not_done) {
     __shared__ double sh[32];
     const DevCase* dc = cases + ids[blockIdx.x];
     double r2 = 0.0, b2 = 0.0;
@@ -152,6 +156,7 @@ __global__ void k_mg_finalize(const DevCase* __restrict__ cases, const int* __re
         st[ST_POT_RESID] = rel;
         const bool done = rel <= tol;
         st[ST_POT_DONE] = done ? 1.0 : 0.0;
+        if (rel > fail_tol) st[ST_POT_FAIL] = 1.0;
         if (first) st[ST_POT_CYCLES] = 0.0;
         if (!done) {
             st[ST_POT_CYCLES] += 1.0;
@@ -352,10 +357,10 @@ cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_mg_finalize(const DevCase* cases, const int* ids, int ncases, double tol, int first,
-                               int* not_done, cudaStream_t st) {
+cudaError_t launch_mg_finalize(const DevCase* cases, const int* ids, int ncases, double tol,
+                               double fail_tol, int first, int* not_done, cudaStream_t st) {
     if (ncases <= 0) return cudaSuccess;
-    k_mg_finalize<<<ncases, 256, 0, st>>>(cases, ids, tol, first, not_done);
+    k_mg_finalize<<<ncases, 256, 0, st>>>(cases, ids, tol, fail_tol, first, not_done);
     return cudaGetLastError();
 }
 
