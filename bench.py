@@ -54,6 +54,8 @@ def workloads():
                   I.config_large()),
         "medium": ("512x256 sessile ferrofluid drop, R=96, vertical field, Bo_m=1.0, chi=1, Ste=0.1",
                    I.config_medium()),
+        "batch": ("64-case seeded sweep (SplitMix64 seed 0): grids 128x64..512x256, R=0.375 ny, "
+                  "field angle 0-90 deg, Bo_m 0-2, Ste 0.05-0.2, chi=1", I.sweep_cases(64, 0)),
     }
 
 
@@ -194,13 +196,21 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     B.build()
-    name, case = workloads()[args.workload]
+    name, work = workloads()[args.workload]
+    cases = work if isinstance(work, list) else [work]
+    case = cases[0]
     prec = lbfs.FP64 if args.precision == "fp64" else lbfs.MIXED
     stream = torch.cuda.current_stream()
-    solver = lbfs.Solver(precision=prec, max_cases=1, device=local, stream=stream.cuda_stream,
-                         torch_alloc=True)
-    solver.set_case(0, case)
-    ncell = case["nx"] * case["ny"]
+    solver = lbfs.Solver(precision=prec, max_cases=len(cases), device=local, stream=stream.cuda_stream,
+                         torch_alloc=True, tile=max(args.tile, 0), use_graph=args.graph)
+    for k, c in enumerate(cases):
+        solver.set_case(k, c)
+    ncell = sum(c["nx"] * c["ny"] for c in cases)
+    solver.step(1)
+    if args.tile >= 0:
+        tile, tile_ms = args.tile, []
+    else:
+        tile, tile_ms = solver.autotune(reps=3)
 
     def barrier():
         torch.cuda.synchronize()
@@ -232,19 +242,24 @@ def run_gpu(args):
     e2e = None
     if not args.no_e2e:
         in_ids = [I.HE, I.P, I.C, I.MX, I.MY, I.FSPREV, I.PHI]
-        state = solver.fields(0, in_ids)
-        pinned = torch.empty((len(in_ids), case["ny"], case["nx"]), dtype=torch.float64, pin_memory=True)
-        host = pinned.numpy()
-        for k, f in enumerate(in_ids):
-            host[k] = state[f]
         out_ids = [I.C, I.FL, I.T]
-        stats_bytes = 80
+        hosts = []
+        for k, c in enumerate(cases):
+            state = solver.fields(k, in_ids)
+            pinned = torch.empty((len(in_ids), c["ny"], c["nx"]), dtype=torch.float64, pin_memory=True)
+            host = pinned.numpy()
+            for q, f in enumerate(in_ids):
+                host[q] = state[f]
+            hosts.append(host)
+        stats_bytes = 80 * len(cases)
         barrier()
         t0 = time.perf_counter()
-        solver.set_fields(0, {f: host[k] for k, f in enumerate(in_ids)})
+        for k, host in enumerate(hosts):
+            solver.set_fields(k, {f: host[q] for q, f in enumerate(in_ids)})
         for _ in range(args.steps):
             solver.step(1)
-        solver.fields(0, out_ids)
+        for k in range(len(cases)):
+            solver.fields(k, out_ids)
         barrier()
         t_e2e = time.perf_counter() - t0
         t_e2e, units_e2e = reduce_over_ranks(t_e2e, ncell * args.steps, world)
@@ -255,9 +270,10 @@ def run_gpu(args):
     # plain FP64 path on the same grid for the mixed-versus-FP64 speed-up
     fp64 = None
     if prec == lbfs.MIXED and args.fp64_steps > 0:
-        s64 = lbfs.Solver(precision=lbfs.FP64, max_cases=1, device=local, stream=stream.cuda_stream,
+        s64 = lbfs.Solver(precision=lbfs.FP64, max_cases=len(cases), device=local, stream=stream.cuda_stream,
                           torch_alloc=True)
-        s64.set_case(0, case)
+        for k, c in enumerate(cases):
+            s64.set_case(k, c)
         s64.step(2)
         barrier()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -293,14 +309,17 @@ def run_gpu(args):
                "sample": f"the same physics on a {sample['nx']}x{sample['ny']} grid "
                          f"(R={sample['radius']:g}), {args.cpu_steps} steps, {dt:.1f} s"}
     state_bytes = ncell * (8 + 4 * (8 if prec == 0 else 4))
+    grid = f"{case['nx']}x{case['ny']}" if len(cases) == 1 else f"{len(cases)} cases, {ncell} cells"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": "f64" if prec == lbfs.FP64 else "f32+f64",
         "data": "synthetic",
-        "config": {"workload": name, "grid": f"{case['nx']}x{case['ny']}",
-                   "precision": args.precision,
+        "config": {"workload": name, "grid": grid, "cases": len(cases),
+                   "precision": args.precision, "graph": bool(args.graph),
+                   "tile": lbfs.TILE_NAMES[tile],
+                   "autotune_ms_per_shape": {nm: round(m, 4) for nm, m in zip(lbfs.TILE_NAMES, tile_ms)},
                    "l2": f"inputs larger than L2 (state {state_bytes / 2**20:.0f} MiB per set, L2 129 MiB)"
                    if state_bytes > L2_BYTES else "L2-resident state"},
         "roofline": roofline,
@@ -324,13 +343,16 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="huge", choices=["huge", "large", "medium"])
+    ap.add_argument("--workload", default="huge", choices=["huge", "large", "medium", "batch"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--cpu-steps", type=int, default=100)
     ap.add_argument("--sample-factor", type=int, default=16)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tile", type=int, default=-1, help="stage tile shape id; -1: autotune")
+    ap.add_argument("--graph", type=int, default=0,
+                    help="1: replay recorded CUDA graphs (disables the per-kernel timing)")
     args = ap.parse_args(argv)
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

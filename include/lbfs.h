@@ -64,7 +64,7 @@ typedef struct lbfs_config {
                                 state is set iterate to it; later mixed steps run at most
                                 one refinement cycle, skipped on the device when the
                                 residual already meets it                                  */
-    int32_t tile;            /* stage-kernel tile shape id (0: the tuned default)           */
+    int32_t tile;            /* stage-kernel tile shape id (see lbfs_autotune); 0: 32 x 8   */
     int32_t reserved[7];
 } lbfs_config;
 
@@ -157,6 +157,16 @@ lbfs_status lbfs_fields(lbfs_ctx* ctx, int32_t case_id, uint32_t mask, double* h
 
 /* Number of device kernel launches the last lbfs_step issued (graph nodes count). */
 int64_t lbfs_last_launch_count(const lbfs_ctx* ctx);
+
+/* Autotuner of the stage kernel's tile shape (the tile is the block's share of the
+ * grid; the halo is fixed at three cells by the stencil).  Times `reps` launches of
+ * each compiled tile shape on the context's current cases (Runge-Kutta stage 2,
+ * which writes only a stage buffer, so the state is untouched), keeps the fastest
+ * for later steps and writes its id to *chosen (nullable).  ms (nullable, n entries)
+ * receives the milliseconds per launch of each shape id < n.  Shapes: 0 32x8,
+ * 1 32x16, 2 64x8, 3 16x16, 4 64x4, 5 16x16 and 6 32x8 with registers cut for a
+ * third resident block per SM (mixed precision). */
+lbfs_status lbfs_autotune(lbfs_ctx* ctx, int32_t reps, int32_t* chosen, double* ms, int32_t n);
 
 /* Kernel timing.  While enabled, lbfs_step brackets every launch with CUDA events on
  * the context's stream and accumulates the elapsed device time per kernel class:

@@ -60,6 +60,7 @@ struct lbfs_ctx {
     double mg_tol = 0.0;
     int mg_max_cycles = 0;
     int half = 0;          // every defined case has dts = 1/2
+    int tile = 0;          // stage-kernel tile shape id (config or autotuner)
     bool pot_fresh = true; // a state was set since the last full potential solve
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
@@ -151,8 +152,8 @@ void harvest(lbfs_ctx* ctx) {
     ctx->ev_pending.clear();
 }
 
-int stage_tw(const lbfs_ctx* ctx) { return stage_tile_w(ctx->prec, ctx->cfg.tile); }
-int stage_th(const lbfs_ctx* ctx) { return stage_tile_h(ctx->prec, ctx->cfg.tile); }
+int stage_tw(const lbfs_ctx* ctx) { return stage_tile_w(ctx->prec, ctx->tile); }
+int stage_th(const lbfs_ctx* ctx) { return stage_tile_h(ctx->prec, ctx->tile); }
 
 // Resolve the case parameters (Eq. 50 groups, mu_c coefficients, boundary flags).
 lbfs_status resolve(lbfs_ctx* ctx, const lbfs_case_desc& d, CaseParams& P) {
@@ -250,8 +251,14 @@ lbfs_status rebuild(lbfs_ctx* ctx) {
     int depth = 0, coarsest = 0;
     int half = 1;
     for (int c = 0; c < (int)ctx->slots.size(); ++c) {
-        const Slot& s = ctx->slots[c];
+        Slot& s = ctx->slots[c];
         if (!s.defined) continue;
+        const int rt = ((s.hd.P.nx + TX - 1) / TX) * ((s.hd.P.ny + TY - 1) / TY);
+        if (rt != s.hd.red_tiles) {
+            s.hd.red_tiles = rt;
+            if (cudaMemcpy(ctx->d_cases + c, &s.hd, sizeof(DevCase), cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(ctx, LBFS_ECUDA, "case table update failed");
+        }
         act.push_back(c);
         if (s.hd.P.dts != 0.5) half = 0;
         int slot = 0;
@@ -380,7 +387,7 @@ lbfs_status one_step(lbfs_ctx* ctx) {
     toc(ctx, LBFS_TIMING_POTENTIAL, t0);
     for (int k = 0; k < 3; ++k) {
         cudaEvent_t t1 = tic(ctx);
-        LK(launch_stage(ctx->prec, ctx->cfg.tile, ctx->half, ctx->d_cases, ctx->d_stage_tiles,
+        LK(launch_stage(ctx->prec, ctx->tile, ctx->half, ctx->d_cases, ctx->d_stage_tiles,
                         ctx->n_stage_tiles, k, ctx->stream));
         toc(ctx, LBFS_TIMING_STAGE, t1);
     }
@@ -450,6 +457,7 @@ lbfs_status lbfs_create(const lbfs_config* cfg, lbfs_ctx** out) {
     ctx->mg_tol = cfg->mg_tol > 0 ? cfg->mg_tol : (ctx->prec == 0 ? 1e-13 : 1e-6);
     ctx->mg_max_cycles = cfg->mg_max_cycles > 0 ? cfg->mg_max_cycles : 40;
     ctx->slots.resize(cfg->max_cases);
+    ctx->tile = (cfg->tile >= 0 && cfg->tile < stage_tile_shapes()) ? cfg->tile : 0;
     if (cfg->cuda_stream) {
         ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
     } else {
@@ -507,6 +515,11 @@ lbfs_status lbfs_set_case(lbfs_ctx* ctx, int32_t id, const lbfs_case_desc* desc)
     fill_phys<double>(P, hd.qd);
     const int TX = stage_tw(ctx), TY = stage_th(ctx);
     hd.red_tiles = ((P.nx + TX - 1) / TX) * ((P.ny + TY - 1) / TY);
+    int red_cap = 0;  // partial-sum slots for the tile shape with the most tiles
+    for (int t = 0; t < stage_tile_shapes(); ++t) {
+        const int w = stage_tile_w(ctx->prec, t), h = stage_tile_h(ctx->prec, t);
+        red_cap = std::max(red_cap, ((P.nx + w - 1) / w) * ((P.ny + h - 1) / h));
+    }
     hd.mg_tiles = ((P.nx + kMgTX - 1) / kMgTX) * ((P.ny + kMgTY - 1) / kMgTY);
     // one device block per case
     const size_t rs = ctx->prec == 0 ? sizeof(double) : sizeof(float);
@@ -535,7 +548,7 @@ lbfs_status lbfs_set_case(lbfs_ctx* ctx, int32_t id, const lbfs_case_desc* desc)
         add(&hd.lev[L].e, lc * rs);
         add(&hd.lev[L].r, lc * rs);
     }
-    add((void**)&hd.red, (size_t)hd.red_tiles * kRedN * sizeof(double));
+    add((void**)&hd.red, (size_t)red_cap * kRedN * sizeof(double));
     add((void**)&hd.mg_red, (size_t)hd.mg_tiles * 2 * sizeof(double));
     Slot& s = ctx->slots[id];
     free_slot(ctx, s);
@@ -680,6 +693,49 @@ lbfs_status lbfs_step(lbfs_ctx* ctx, int32_t nsteps, lbfs_case_stats* out) {
 }
 
 int64_t lbfs_last_launch_count(const lbfs_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+lbfs_status lbfs_autotune(lbfs_ctx* ctx, int32_t reps, int32_t* chosen, double* ms, int32_t n) {
+    if (!ctx || reps < 1 || n < 0) return LBFS_EINVAL;
+    if (ctx->dirty) {
+        lbfs_status r = rebuild(ctx);
+        if (r != LBFS_OK) return r;
+    }
+    if (ctx->n_active == 0) return fail(ctx, LBFS_EINVAL, "no case defined");
+    CK(cudaSetDevice(ctx->cfg.device));
+    cudaEvent_t a = take_event(ctx), b = take_event(ctx);
+    int best = ctx->tile;
+    double best_ms = 1e300;
+    for (int t = 0; t < stage_tile_shapes(); ++t) {
+        ctx->tile = t;
+        lbfs_status r = rebuild(ctx);
+        if (r != LBFS_OK) return r;
+        // Runge-Kutta stage 2 reads sets 0 and 1 and dF_s/dt and writes only the stage
+        // buffer 2, so timing it leaves the state untouched
+        CK(launch_stage(ctx->prec, t, ctx->half, ctx->d_cases, ctx->d_stage_tiles, ctx->n_stage_tiles, 1,
+                        ctx->stream));
+        CK(cudaEventRecord(a, ctx->stream));
+        for (int k = 0; k < reps; ++k)
+            CK(launch_stage(ctx->prec, t, ctx->half, ctx->d_cases, ctx->d_stage_tiles, ctx->n_stage_tiles, 1,
+                            ctx->stream));
+        CK(cudaEventRecord(b, ctx->stream));
+        CK(cudaEventSynchronize(b));
+        float el = 0.f;
+        CK(cudaEventElapsedTime(&el, a, b));
+        const double per = el / reps;
+        if (t < n && ms) ms[t] = per;
+        if (per < best_ms) {
+            best_ms = per;
+            best = t;
+        }
+    }
+    ctx->ev_pool.push_back(a);
+    ctx->ev_pool.push_back(b);
+    ctx->tile = best;
+    lbfs_status r = rebuild(ctx);
+    if (r != LBFS_OK) return r;
+    if (chosen) *chosen = best;
+    return LBFS_OK;
+}
 
 lbfs_status lbfs_timing(lbfs_ctx* ctx, int32_t enable) {
     if (!ctx) return LBFS_EINVAL;

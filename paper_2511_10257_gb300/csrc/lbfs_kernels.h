@@ -9,6 +9,7 @@
 namespace lbfs {
 
 // stage kernel (lbfs_stage.cu); prec 0 = FP64, 1 = mixed
+int stage_tile_shapes();
 int stage_tile_w(int prec, int tile);
 int stage_tile_h(int prec, int tile);
 // half: every case streams half a cell (dts = 1/2), which selects the reconstruction

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         const R rinv = R(3) / rho;
         R u = gMx[gi] * rinv, v = gMy[gi] * rinv;
         R phi = gPhi[gi];
-        R Hes = R(He);
+        R Hes = R(He);   // H_e for the reconstruction (enters only the interface T_f)
         if (wall >= 0) {
             u = -u;
             v = -v;
@@ -510,27 +510,57 @@ static cudaError_t launch_t(const DevCase* cases, const TileRef* tiles, int ntil
     return cudaGetLastError();
 }
 
+// Tile shapes the autotuner chooses from (id -> TX x TY cells per block, and the
+// number of blocks per SM the register budget is cut for).  All have at least 256
+// cells, so a case never has more stage tiles than with 16 x 16.
+static constexpr int kShapes = 7;
+static constexpr int kShapeW[kShapes] = {32, 32, 64, 16, 64, 16, 32};
+static constexpr int kShapeH[kShapes] = {8, 16, 8, 16, 4, 16, 8};
+
+int stage_tile_shapes() { return kShapes; }
 int stage_tile_w(int prec, int tile) {
     (void)prec;
-    (void)tile;
-    return 32;
+    return kShapeW[(tile >= 0 && tile < kShapes) ? tile : 0];
 }
 int stage_tile_h(int prec, int tile) {
     (void)prec;
-    (void)tile;
-    return 8;
+    return kShapeH[(tile >= 0 && tile < kShapes) ? tile : 0];
+}
+
+template <class R, int MINB_SMALL, int MINB_X>
+static cudaError_t launch_prec(int tile, int half, const DevCase* cases, const TileRef* tiles, int ntiles,
+                               int stage, cudaStream_t st) {
+    constexpr bool T = true, F = false;
+    switch (tile) {
+    case 1:
+        return half ? launch_t<R, double, 32, 16, 1, T>(cases, tiles, ntiles, stage, st)
+                    : launch_t<R, double, 32, 16, 1, F>(cases, tiles, ntiles, stage, st);
+    case 2:
+        return half ? launch_t<R, double, 64, 8, 1, T>(cases, tiles, ntiles, stage, st)
+                    : launch_t<R, double, 64, 8, 1, F>(cases, tiles, ntiles, stage, st);
+    case 3:
+        return half ? launch_t<R, double, 16, 16, MINB_SMALL, T>(cases, tiles, ntiles, stage, st)
+                    : launch_t<R, double, 16, 16, MINB_SMALL, F>(cases, tiles, ntiles, stage, st);
+    case 4:
+        return half ? launch_t<R, double, 64, 4, MINB_SMALL, T>(cases, tiles, ntiles, stage, st)
+                    : launch_t<R, double, 64, 4, MINB_SMALL, F>(cases, tiles, ntiles, stage, st);
+    case 5:
+        return half ? launch_t<R, double, 16, 16, MINB_X, T>(cases, tiles, ntiles, stage, st)
+                    : launch_t<R, double, 16, 16, MINB_X, F>(cases, tiles, ntiles, stage, st);
+    case 6:
+        return half ? launch_t<R, double, 32, 8, MINB_X, T>(cases, tiles, ntiles, stage, st)
+                    : launch_t<R, double, 32, 8, MINB_X, F>(cases, tiles, ntiles, stage, st);
+    default:
+        return half ? launch_t<R, double, 32, 8, MINB_SMALL, T>(cases, tiles, ntiles, stage, st)
+                    : launch_t<R, double, 32, 8, MINB_SMALL, F>(cases, tiles, ntiles, stage, st);
+    }
 }
 
 cudaError_t launch_stage(int prec, int tile, int half, const DevCase* cases, const TileRef* tiles,
                          int ntiles, int stage, cudaStream_t st) {
-    (void)tile;
     if (ntiles <= 0) return cudaSuccess;
-    if (prec == 0) {
-        if (half) return launch_t<double, double, 32, 8, 1, true>(cases, tiles, ntiles, stage, st);
-        return launch_t<double, double, 32, 8, 1, false>(cases, tiles, ntiles, stage, st);
-    }
-    if (half) return launch_t<float, double, 32, 8, 2, true>(cases, tiles, ntiles, stage, st);
-    return launch_t<float, double, 32, 8, 2, false>(cases, tiles, ntiles, stage, st);
+    if (prec == 0) return launch_prec<double, 1, 1>(tile, half, cases, tiles, ntiles, stage, st);
+    return launch_prec<float, 2, 3>(tile, half, cases, tiles, ntiles, stage, st);
 }
 
 }  // namespace lbfs

@@ -67,8 +67,10 @@ class CaseStats(ct.Structure):
 
 
 EXPORTS = ("lbfs_create", "lbfs_set_case", "lbfs_set_fields", "lbfs_step", "lbfs_fields",
-           "lbfs_last_launch_count", "lbfs_timing", "lbfs_timing_read", "lbfs_destroy",
-           "lbfs_last_error")
+           "lbfs_last_launch_count", "lbfs_timing", "lbfs_timing_read", "lbfs_autotune",
+           "lbfs_destroy", "lbfs_last_error")
+TILE_SHAPES = [(32, 8), (32, 16), (64, 8), (16, 16), (64, 4), (16, 16), (32, 8)]
+TILE_NAMES = ["32x8", "32x16", "64x8", "16x16", "64x4", "16x16/3", "32x8/3"]
 TIMING_STAGE, TIMING_POTENTIAL, TIMING_FINALIZE = range(3)
 
 _lib = None
@@ -95,9 +97,10 @@ def load(path: str = LIB_PATH):
     L.lbfs_last_error.argtypes = [vp]
     L.lbfs_last_error.restype = ct.c_char_p
     L.lbfs_timing.argtypes = [vp, ct.c_int32]
+    L.lbfs_autotune.argtypes = [vp, ct.c_int32, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_double), ct.c_int32]
     L.lbfs_timing_read.argtypes = [vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int32]
     for name in ("lbfs_create", "lbfs_set_case", "lbfs_set_fields", "lbfs_step", "lbfs_fields",
-                 "lbfs_timing", "lbfs_timing_read"):
+                 "lbfs_timing", "lbfs_timing_read", "lbfs_autotune"):
         getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -219,6 +222,15 @@ class Solver:
 
     def last_launch_count(self) -> int:
         return int(self._L.lbfs_last_launch_count(self._h))
+
+    def autotune(self, reps: int = 5):
+        """time every stage tile shape on the current cases and keep the fastest;
+        returns (chosen id, [ms per launch for each shape])"""
+        n = len(TILE_SHAPES)
+        chosen = ct.c_int32()
+        ms = (ct.c_double * n)()
+        self._check(self._L.lbfs_autotune(self._h, int(reps), ct.byref(chosen), ms, n))
+        return chosen.value, list(ms)
 
     def timing(self, enable: bool):
         self._check(self._L.lbfs_timing(self._h, 1 if enable else 0))

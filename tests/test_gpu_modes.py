@@ -99,3 +99,33 @@ def test_mixed_precision_conserves_phase_field_mass():
     c1 = s.step(2000)[0]["sum_C"]
     s.close()
     assert abs(c1 - c0) <= 2e-6 * c0
+
+
+@pytest.mark.parametrize("precision", [lbfs.MIXED, lbfs.FP64])
+def test_tile_shapes_give_identical_fields(precision):
+    """Every face is computed with the same arithmetic whichever tile holds it, so all
+    tile shapes give bitwise-identical fields; the autotuner keeps one of them."""
+    c = I.case(100, 52, radius=19.0, bo_m=1.2, field_angle_deg=20.0, stefan=0.25)
+    ref = None
+    for tile in range(len(lbfs.TILE_SHAPES)):
+        s = lbfs.Solver(precision=precision, max_cases=1, tile=tile)
+        s.set_case(0, c)
+        s.step(15)
+        got = s.fields(0, IDS)
+        if tile == 0:
+            chosen, ms = s.autotune(reps=2)
+            assert 0 <= chosen < len(lbfs.TILE_SHAPES) and all(m > 0 for m in ms)
+            s.step(5)
+            after = s.fields(0, IDS)
+        s.close()
+        if ref is None:
+            ref = got
+        for f in IDS:
+            assert np.array_equal(got[f], ref[f]), (tile, I.FIELD_NAMES[f])
+    s = lbfs.Solver(precision=precision, max_cases=1)
+    s.set_case(0, c)
+    s.step(20)
+    plain = s.fields(0, IDS)
+    s.close()
+    for f in IDS:
+        assert np.array_equal(after[f], plain[f]), I.FIELD_NAMES[f]
