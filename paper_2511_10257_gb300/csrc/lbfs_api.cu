@@ -17,7 +17,6 @@ namespace {
 
 constexpr int kCoarsenCells = 256;    // stop coarsening at or below this many cells
 constexpr int kCoarsestMax = 4096;    // largest coarsest level the one-block CG accepts
-constexpr int kNu = 2;                // pre- and post-smoothing sweeps (red + black)
 
 size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -42,6 +41,8 @@ struct lbfs_ctx {
     int n_stage_tiles = 0;
     std::vector<TileRef*> d_mg_tiles;
     std::vector<int> n_mg_tiles;
+    std::vector<TileRef*> d_ft_tiles;   // fused V-cycle tiles per level
+    std::vector<int> n_ft_tiles;
     int* d_active = nullptr;
     int n_active = 0;
     int* d_pot = nullptr;
@@ -271,7 +272,7 @@ lbfs_status rebuild(lbfs_ctx* ctx) {
             coarsest = std::max(coarsest, lc.nx * lc.ny);
         }
     }
-    std::vector<std::vector<TileRef>> mg(depth);
+    std::vector<std::vector<TileRef>> mg(depth), ft(depth);
     for (int L = 0; L < depth; ++L)
         for (int c : pot) {
             const Slot& s = ctx->slots[c];
@@ -279,6 +280,11 @@ lbfs_status rebuild(lbfs_ctx* ctx) {
             int slot = 0;
             for (int y = 0; y < s.hd.lev[L].ny; y += kMgTY)
                 for (int x = 0; x < s.hd.lev[L].nx; x += kMgTX) mg[L].push_back(TileRef{c, x, y, slot++});
+            if (s.hd.nlev - 1 > L) {
+                slot = 0;
+                for (int y = 0; y < s.hd.lev[L].ny; y += kFusedTY)
+                    for (int x = 0; x < s.hd.lev[L].nx; x += kFusedTX) ft[L].push_back(TileRef{c, x, y, slot++});
+            }
         }
     auto upload = [&](void** dst, const void* src, size_t bytes) -> bool {
         if (*dst) dfree(ctx, *dst);
@@ -293,12 +299,17 @@ lbfs_status rebuild(lbfs_ctx* ctx) {
         !upload((void**)&ctx->d_pot, pot.data(), pot.size() * sizeof(int)))
         return fail(ctx, LBFS_ENOMEM, "tile list upload failed");
     for (auto* p : ctx->d_mg_tiles) dfree(ctx, p);
+    for (auto* p : ctx->d_ft_tiles) dfree(ctx, p);
     ctx->d_mg_tiles.assign(depth, nullptr);
     ctx->n_mg_tiles.assign(depth, 0);
+    ctx->d_ft_tiles.assign(depth, nullptr);
+    ctx->n_ft_tiles.assign(depth, 0);
     for (int L = 0; L < depth; ++L) {
-        if (!upload((void**)&ctx->d_mg_tiles[L], mg[L].data(), mg[L].size() * sizeof(TileRef)))
+        if (!upload((void**)&ctx->d_mg_tiles[L], mg[L].data(), mg[L].size() * sizeof(TileRef)) ||
+            !upload((void**)&ctx->d_ft_tiles[L], ft[L].data(), ft[L].size() * sizeof(TileRef)))
             return fail(ctx, LBFS_ENOMEM, "multigrid tile list upload failed");
         ctx->n_mg_tiles[L] = (int)mg[L].size();
+        ctx->n_ft_tiles[L] = (int)ft[L].size();
     }
     ctx->n_stage_tiles = (int)st.size();
     ctx->n_active = (int)act.size();
@@ -318,25 +329,18 @@ lbfs_status rebuild(lbfs_ctx* ctx) {
             return fail(ctx, LBFS_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
     } while (0)
 
+// One V-cycle on the correction equation A e = r of every solving case: a fused
+// pre-smooth + restriction kernel per level on the way down, the one-block CG on each
+// case's coarsest level, a fused prolongation + post-smooth kernel per level up.
 lbfs_status vcycle(lbfs_ctx* ctx) {
     const int p = ctx->prec;
     cudaStream_t s = ctx->stream;
     const int D = ctx->max_depth;
-    for (int L = 0; L + 1 < D; ++L) {
-        for (int k = 0; k < kNu; ++k) {
-            LK(launch_mg_smooth(p, ctx->d_cases, ctx->d_mg_tiles[L], ctx->n_mg_tiles[L], L, 0, s));
-            LK(launch_mg_smooth(p, ctx->d_cases, ctx->d_mg_tiles[L], ctx->n_mg_tiles[L], L, 1, s));
-        }
-        LK(launch_mg_restrict_resid(p, ctx->d_cases, ctx->d_mg_tiles[L + 1], ctx->n_mg_tiles[L + 1], L + 1, s));
-    }
+    for (int L = 0; L + 1 < D; ++L)
+        LK(launch_mg_vdown(p, ctx->d_cases, ctx->d_ft_tiles[L], ctx->n_ft_tiles[L], L, s));
     LK(launch_mg_coarsest(p, ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->coarsest_cells, s));
-    for (int L = D - 2; L >= 0; --L) {
-        LK(launch_mg_prolong(p, ctx->d_cases, ctx->d_mg_tiles[L], ctx->n_mg_tiles[L], L, s));
-        for (int k = 0; k < kNu; ++k) {
-            LK(launch_mg_smooth(p, ctx->d_cases, ctx->d_mg_tiles[L], ctx->n_mg_tiles[L], L, 0, s));
-            LK(launch_mg_smooth(p, ctx->d_cases, ctx->d_mg_tiles[L], ctx->n_mg_tiles[L], L, 1, s));
-        }
-    }
+    for (int L = D - 2; L >= 0; --L)
+        LK(launch_mg_vup(p, ctx->d_cases, ctx->d_ft_tiles[L], ctx->n_ft_tiles[L], L, s));
     return LBFS_OK;
 }
 
@@ -537,8 +541,12 @@ lbfs_status lbfs_set_case(lbfs_ctx* ctx, int32_t id, const lbfs_case_desc* desc)
         add(&hd.my[k], cells * rs);
         add(&hd.C[k], cells * rs);
     }
-    add((void**)&hd.phi64, cells * sizeof(double));
-    if (ctx->prec != 0) add(&hd.phi, cells * rs);
+    if (ctx->prec == 0) {
+        add((void**)&hd.phi64, cells * sizeof(double));
+    } else {
+        add(&hd.phi, cells * rs);
+        add((void**)&hd.phi_lo, cells * sizeof(float));
+    }
     add(&hd.Fs_prev, cells * rs);
     add(&hd.Sdot, cells * rs);
     for (int L = 0; L < nlev; ++L) {
@@ -768,6 +776,7 @@ void lbfs_destroy(lbfs_ctx* ctx) {
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
     for (Slot& s : ctx->slots) free_slot(ctx, s);
     for (auto* p : ctx->d_mg_tiles) dfree(ctx, p);
+    for (auto* p : ctx->d_ft_tiles) dfree(ctx, p);
     dfree(ctx, ctx->d_stage_tiles);
     dfree(ctx, ctx->d_active);
     dfree(ctx, ctx->d_pot);

@@ -36,9 +36,7 @@ __global__ void k_init(const DevCase* __restrict__ dc, InitArgs a) {
     static_cast<R*>(dc->mx[0])[k] = R(0);
     static_cast<R*>(dc->my[0])[k] = R(0);
     static_cast<R*>(dc->C[0])[k] = R(C);
-    const double phi = -P.H0 * (x * P.cos_t + y * P.sin_t);
-    dc->phi64[k] = phi;
-    static_cast<R*>(dc->phi)[k] = R(phi);
+    phi_set<R>(dc, k, -P.H0 * (x * P.cos_t + y * P.sin_t));
     R T, Fl;
     invert_enthalpy<R, double>(P, He, R(C), T, Fl);
     static_cast<R*>(dc->Fs_prev)[k] = R(1) - Fl;
@@ -86,7 +84,7 @@ __global__ void k_derive(const DevCase* __restrict__ dc, uint32_t mask, double* 
         if (!(mask & (1u << f))) continue;
         double v = 0.0;
         switch (f) {
-        case 0: v = dc->phi64[k]; break;
+        case 0: v = phi_get<R>(dc, k); break;
         case 1: v = He; break;
         case 2: v = (double)T; break;
         case 3: v = (double)Fl; break;
@@ -122,10 +120,7 @@ __global__ void k_store(const DevCase* __restrict__ dc, uint32_t mask, const dou
         if (!(mask & (1u << f))) continue;
         const double v = in[slot * N + o];
         switch (f) {
-        case 0:
-            dc->phi64[k] = v;
-            static_cast<R*>(dc->phi)[k] = R(v);
-            break;
+        case 0: phi_set<R>(dc, k, v); break;
         case 1: static_cast<double*>(dc->He[0])[k] = v; break;
         case 4: static_cast<R*>(dc->p[0])[k] = R(v); break;
         case 7: static_cast<R*>(dc->C[0])[k] = R(v); break;

@@ -58,8 +58,9 @@ struct DevCase {
     void* mx[3];
     void* my[3];
     void* C[3];
-    void* phi;        // R copy of the potential read by the stage kernel
-    double* phi64;    // FP64 master potential (== phi in FP64 mode)
+    void* phi;        // potential read by the stage kernel (R); FP64 mode: the master
+    double* phi64;    // FP64 mode: the master potential (== phi); mixed: unused
+    float* phi_lo;    // mixed: low word of the master potential phi + phi_lo (FP32 pair)
     void* Fs_prev;    // R: F_s of the previous step, replaced by F_s^n in stage 1
     void* Sdot;       // R: lagged dF_s/dt of the current step, written by stage 1
     PhysT<float> qf;
@@ -155,6 +156,50 @@ template <>
 __device__ __forceinline__ const PhysT<float>& phys_of<float>(const DevCase* dc) { return dc->qf; }
 template <>
 __device__ __forceinline__ const PhysT<double>& phys_of<double>(const DevCase* dc) { return dc->qd; }
+
+// ---- FP64-accurate arithmetic on FP32 pairs (hi + lo, |lo| <= ulp(hi)/2) ---------
+// Error-free transformations: two_sum (Knuth), two_prod (FMA).  Explicit round-to-
+// nearest intrinsics keep the compiler from contracting or reordering them.
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ void two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = __fmaf_rn(a, b, -p);
+}
+// (sh, sl) += (ph, pl), renormalised
+__device__ __forceinline__ void pair_add(float& sh, float& sl, float ph, float pl) {
+    float s, e;
+    two_sum(sh, ph, s, e);
+    e = __fadd_rn(e, __fadd_rn(sl, pl));
+    sh = __fadd_rn(s, e);
+    sl = __fsub_rn(e, __fsub_rn(sh, s));
+}
+// split a double into the nearest FP32 pair
+__device__ __forceinline__ void pair_from(double v, float& h, float& l) {
+    h = (float)v;
+    l = (float)(v - (double)h);
+}
+
+// master potential of cell k in FP64, whichever precision stores it
+template <class R>
+__device__ __forceinline__ double phi_get(const DevCase* dc, size_t k) {
+    if (sizeof(R) == 8) return dc->phi64[k];
+    return (double)static_cast<const float*>(dc->phi)[k] + (double)dc->phi_lo[k];
+}
+template <class R>
+__device__ __forceinline__ void phi_set(const DevCase* dc, size_t k, double v) {
+    if (sizeof(R) == 8) {
+        dc->phi64[k] = v;
+    } else {
+        float h, l;
+        pair_from(v, h, l);
+        static_cast<float*>(dc->phi)[k] = h;
+        dc->phi_lo[k] = l;
+    }
+}
 
 template <class R>
 __device__ __forceinline__ R load(const void* base, size_t idx) {

@@ -26,17 +26,17 @@ cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* 
 // tol: the convergence test; a residual above fail_tol marks the case's solve failed
 cudaError_t launch_mg_finalize(const DevCase* cases, const int* case_ids, int ncases, double tol,
                                double fail_tol, int first, int* not_done, cudaStream_t st);
-cudaError_t launch_mg_smooth(int prec, const DevCase* cases, const TileRef* tiles, int n, int level,
-                             int color, cudaStream_t st);
-cudaError_t launch_mg_restrict_resid(int prec, const DevCase* cases, const TileRef* tiles, int n,
-                                     int level_coarse, cudaStream_t st);
-cudaError_t launch_mg_prolong(int prec, const DevCase* cases, const TileRef* tiles, int n, int level,
-                              cudaStream_t st);
 cudaError_t launch_mg_coarsest(int prec, const DevCase* cases, const int* case_ids, int ncases,
                                int max_cells, cudaStream_t st);
 cudaError_t launch_mg_correct(int prec, const DevCase* cases, const TileRef* tiles, int n,
                               cudaStream_t st);
 size_t mg_coarsest_smem(int prec, int max_cells);
+// fused V-cycle legs over 32 x 16 tiles of one level (kFusedTX x kFusedTY)
+constexpr int kFusedTX = 32, kFusedTY = 16;
+cudaError_t launch_mg_vdown(int prec, const DevCase* cases, const TileRef* tiles, int n, int level,
+                            cudaStream_t st);
+cudaError_t launch_mg_vup(int prec, const DevCase* cases, const TileRef* tiles, int n, int level,
+                          cudaStream_t st);
 
 // per-case utility kernels (lbfs_fields.cu)
 struct InitArgs {

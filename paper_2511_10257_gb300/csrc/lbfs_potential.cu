@@ -87,8 +87,83 @@ __global__ void __launch_bounds__(kNT) k_restrict_mu(const DevCase* __restrict__
         M(0.25) * ((mf[k0] + mf[k0 + 1]) + (mf[k0 + f.pitch] + mf[k0 + f.pitch + 1]));
 }
 
-// FP64 residual of the master potential on the fine level; zeroes the correction;
-// per-tile partial sums of |r|^2 and |b|^2.
+// FP64-accurate residual of the master potential on the fine level, zeroes the
+// correction, and per-tile partial sums of |r|^2 and |b|^2.
+//   r = b - A phi = -[sum_nb mu_f (phi_c - phi_nb) + sum_Dirichlet 2 mu_c (phi_c - phi_w)]
+// FP64 mode: in FP64.  Mixed mode: the master potential is the FP32 pair phi + phi_lo
+// and the differences, products and sums are error-free pair operations on the FP32
+// pipes (about 2^-48 relative), because FP64 issue is scarce on GB300; only the norms
+// are accumulated in FP64.
+template <class M>
+__device__ __forceinline__ double residual_cell(const DevCase* dc, const CaseParams& P, const MGLevel& lv,
+                                                int i, int j, double& b_out);
+
+template <>
+__device__ __forceinline__ double residual_cell<double>(const DevCase* dc, const CaseParams& P,
+                                                        const MGLevel& lv, int i, int j, double& b_out) {
+    const double* mu = static_cast<const double*>(lv.mu);
+    const double* ph = dc->phi64;
+    const size_t k = (size_t)j * lv.pitch + i;
+    const double mc = mu[k], pc = ph[k];
+    double diag = 0.0, off = 0.0, b = 0.0;
+    for (int w = 0; w < 4; ++w) {
+        int ii, jj;
+        if (neighbour(P, lv.nx, lv.ny, i, j, w, ii, jj)) {
+            const size_t kn = (size_t)jj * lv.pitch + ii;
+            const double mf = 0.5 * (mc + mu[kn]);
+            diag += mf;
+            off += mf * ph[kn];
+        } else if (P.mag_dir[w]) {
+            const double wx = w == 0 ? 0.0 : (w == 1 ? (double)lv.nx : i + 0.5);
+            const double wy = w == 2 ? 0.0 : (w == 3 ? (double)lv.ny : j + 0.5);
+            const double pw = -P.H0 * (wx * P.cos_t + wy * P.sin_t);
+            diag += 2.0 * mc;
+            b += 2.0 * mc * pw;
+        }
+    }
+    b_out = b;
+    return b - (diag * pc - off);
+}
+
+template <>
+__device__ __forceinline__ double residual_cell<float>(const DevCase* dc, const CaseParams& P,
+                                                       const MGLevel& lv, int i, int j, double& b_out) {
+    const float* mu = static_cast<const float*>(lv.mu);
+    const float* hi = static_cast<const float*>(dc->phi);
+    const float* lo = dc->phi_lo;
+    const size_t k = (size_t)j * lv.pitch + i;
+    const float mc = mu[k], hc = hi[k], lc = lo[k];
+    float ah = 0.f, al = 0.f;   // A phi as a pair
+    double b = 0.0;
+    for (int w = 0; w < 4; ++w) {
+        int ii, jj;
+        float c, nh, nl;
+        if (neighbour(P, lv.nx, lv.ny, i, j, w, ii, jj)) {
+            const size_t kn = (size_t)jj * lv.pitch + ii;
+            c = 0.5f * (mc + mu[kn]);
+            nh = hi[kn];
+            nl = lo[kn];
+        } else if (P.mag_dir[w]) {
+            const double wx = w == 0 ? 0.0 : (w == 1 ? (double)lv.nx : i + 0.5);
+            const double wy = w == 2 ? 0.0 : (w == 3 ? (double)lv.ny : j + 0.5);
+            const double pw = -P.H0 * (wx * P.cos_t + wy * P.sin_t);
+            c = 2.f * mc;
+            pair_from(pw, nh, nl);
+            b += (double)c * pw;
+        } else {
+            continue;
+        }
+        float dh, de, p, pe;
+        two_sum(hc, -nh, dh, de);
+        const float dl = __fadd_rn(de, __fsub_rn(lc, nl));
+        two_prod(c, dh, p, pe);
+        pe = __fmaf_rn(c, dl, pe);
+        pair_add(ah, al, p, pe);
+    }
+    b_out = b;
+    return (double)(-__fadd_rn(ah, al));
+}
+
 template <class M>
 __global__ void __launch_bounds__(kNT) k_residual64(const DevCase* __restrict__ cases,
                                                     const TileRef* __restrict__ tiles) {
@@ -100,34 +175,17 @@ __global__ void __launch_bounds__(kNT) k_residual64(const DevCase* __restrict__ 
     const int i = tr.x0 + threadIdx.x % kMgTX, j = tr.y0 + threadIdx.x / kMgTX;
     double r2 = 0.0, b2 = 0.0;
     if (i < lv.nx && j < lv.ny) {
-        const M* mu = static_cast<const M*>(lv.mu);
-        const double* ph = dc->phi64;
+        double b;
+        const double r = residual_cell<M>(dc, P, lv, i, j, b);
         const size_t k = (size_t)j * lv.pitch + i;
-        const M mcm = mu[k];
-        const double pc = ph[k];
-        // face coefficients in M (they are M-precision data), potentials and the
-        // accumulation of the residual in FP64
-        M diag = 0;
-        double off = 0.0, b = 0.0;
-        for (int w = 0; w < 4; ++w) {
-            int ii, jj;
-            if (neighbour(P, lv.nx, lv.ny, i, j, w, ii, jj)) {
-                const size_t kn = (size_t)jj * lv.pitch + ii;
-                const M mf = M(0.5) * (mcm + mu[kn]);
-                diag += mf;
-                off += (double)mf * ph[kn];
-            } else if (P.mag_dir[w]) {
-                const double wx = w == 0 ? 0.0 : (w == 1 ? (double)lv.nx : i + 0.5);
-                const double wy = w == 2 ? 0.0 : (w == 3 ? (double)lv.ny : j + 0.5);
-                const double pw = -P.H0 * (wx * P.cos_t + wy * P.sin_t);
-                diag += M(2) * mcm;
-                b += 2.0 * (double)mcm * pw;
-            }
-        }
-        const double r = b - ((double)diag * pc - off);
         static_cast<M*>(lv.r)[k] = M(r);
         static_cast<M*>(lv.e)[k] = M(0);
-        r2 = r * r;
+        if (sizeof(M) == 8) {
+            r2 = r * r;
+        } else {
+            const float rf = (float)r;
+            r2 = (double)(rf * rf);
+        }
         b2 = b * b;
     }
     r2 = block_sum(r2, sh);
@@ -165,61 +223,6 @@ __global__ void k_mg_finalize(const DevCase* __restrict__ cases, const int* __re
     }
 }
 
-template <class M>
-__global__ void __launch_bounds__(kNT) k_smooth(const DevCase* __restrict__ cases,
-                                                const TileRef* __restrict__ tiles, int L, int color) {
-    const TileRef tr = tiles[blockIdx.x];
-    const DevCase* dc = cases + tr.case_id;
-    if (pot_done(dc) || L >= dc->nlev - 1) return;
-    const CaseParams& P = dc->P;
-    const MGLevel lv = dc->lev[L];
-    const int i = tr.x0 + threadIdx.x % kMgTX, j = tr.y0 + threadIdx.x / kMgTX;
-    if (i >= lv.nx || j >= lv.ny || ((i + j) & 1) != color) return;
-    const M* mu = static_cast<const M*>(lv.mu);
-    M* e = static_cast<M*>(lv.e);
-    const size_t k = (size_t)j * lv.pitch + i;
-    const M mc = mu[k];
-    M diag = 0, off = 0;
-#pragma unroll
-    for (int w = 0; w < 4; ++w) {
-        int ii, jj;
-        if (neighbour(P, lv.nx, lv.ny, i, j, w, ii, jj)) {
-            const size_t kn = (size_t)jj * lv.pitch + ii;
-            const M mf = M(0.5) * (mc + mu[kn]);
-            diag += mf;
-            off += mf * e[kn];
-        } else if (P.mag_dir[w]) {
-            diag += M(2) * mc;
-        }
-    }
-    e[k] = (static_cast<const M*>(lv.r)[k] + off) / diag;
-}
-
-// coarse residual r_L = sum over the four children of (r - A e) on level L-1; e_L = 0
-template <class M>
-__global__ void __launch_bounds__(kNT) k_restrict_resid(const DevCase* __restrict__ cases,
-                                                        const TileRef* __restrict__ tiles, int L) {
-    const TileRef tr = tiles[blockIdx.x];
-    const DevCase* dc = cases + tr.case_id;
-    if (pot_done(dc)) return;
-    const CaseParams& P = dc->P;
-    const MGLevel c = dc->lev[L], f = dc->lev[L - 1];
-    const int I = tr.x0 + threadIdx.x % kMgTX, J = tr.y0 + threadIdx.x / kMgTX;
-    if (I >= c.nx || J >= c.ny) return;
-    const M* mu = static_cast<const M*>(f.mu);
-    const M* e = static_cast<const M*>(f.e);
-    const M* r = static_cast<const M*>(f.r);
-    M acc = 0;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int i = 2 * I + (q & 1), j = 2 * J + (q >> 1);
-        acc += r[(size_t)j * f.pitch + i] - apply_A<M>(P, mu, e, f.nx, f.ny, f.pitch, i, j);
-    }
-    const size_t kc = (size_t)J * c.pitch + I;
-    static_cast<M*>(c.r)[kc] = acc;
-    static_cast<M*>(c.e)[kc] = M(0);
-}
-
 // coarse value at (I, J), possibly one cell outside: periodic wrap, Dirichlet wall
 // (homogeneous) mirrors with a sign change, an insulating wall mirrors evenly
 template <class M>
@@ -247,24 +250,193 @@ __device__ __forceinline__ M coarse_at(const CaseParams& P, const M* e, int nx, 
     return sgn * e[(size_t)J * pitch + I];
 }
 
+// ---- fused V-cycle legs ------------------------------------------------------
+// A block owns a kFTX x kFTY tile of one level and keeps it with a halo in shared
+// memory.  Red-black Gauss-Seidel half-sweeps shrink the valid region by one cell
+// each, so after kFNu full sweeps the tile (plus one cell) holds exactly the values the
+// sweeps over the whole level would give.  Down leg: pre-smooth from e = 0, store e,
+// restrict r - A e to the next level.  Up leg: add the bilinear prolongation of the
+// coarse correction, post-smooth, store e.
+constexpr int kFTX = 32, kFTY = 16, kFNu = 2;
+constexpr int kHD = 2 * kFNu + 1, kHU = 2 * kFNu;
+
+template <int H>
+struct FRegion {
+    static constexpr int W = kFTX + 2 * H, Hh = kFTY + 2 * H, N = W * Hh;
+};
+
+// global position of region cell k of a tile at (x0, y0) with halo H; returns 0 if it
+// lies beyond a non-periodic wall, else 1 with (sx, sy) the (wrapped) source cell
+__device__ __forceinline__ int region_source(const CaseParams& P, int nx, int ny, int x0, int y0, int H,
+                                             int W, int k, int& gx, int& gy, int& sx, int& sy) {
+    gx = x0 - H + k % W;
+    gy = y0 - H + k / W;
+    sx = gx;
+    sy = gy;
+    if (sx < 0 || sx >= nx) {
+        if (!P.periodic_x) return 0;
+        sx = ((sx % nx) + nx) % nx;
+    }
+    if (sy < 0 || sy >= ny) {
+        if (!P.periodic_y) return 0;
+        sy = ((sy % ny) + ny) % ny;
+    }
+    return 1;
+}
+
+// one red-black half-sweep of colour c over the region cells at least h from its edge
+template <class M, int H>
+__device__ __forceinline__ void region_half_sweep(const CaseParams& P, int nx, int ny, int x0, int y0,
+                                                  const M* mu, const M* r, M* e,
+                                                  const unsigned char* in, int c, int h) {
+    using G = FRegion<H>;
+    for (int k = threadIdx.x; k < G::N; k += blockDim.x) {
+        const int lx = k % G::W, ly = k / G::W;
+        if (lx < h || lx >= G::W - h || ly < h || ly >= G::Hh - h || !in[k]) continue;
+        const int gx = x0 - H + lx, gy = y0 - H + ly;
+        if (((gx + gy) & 1) != c) continue;
+        const M mc = mu[k];
+        M diag = 0, off = 0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            int ii, jj;
+            if (neighbour(P, nx, ny, gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx),
+                          gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy), w, ii, jj)) {
+                const int kn = k + (w == 0 ? -1 : w == 1 ? 1 : w == 2 ? -G::W : G::W);
+                const M mf = M(0.5) * (mc + mu[kn]);
+                diag += mf;
+                off += mf * e[kn];
+            } else if (P.mag_dir[w]) {
+                diag += M(2) * mc;
+            }
+        }
+        e[k] = (r[k] + off) / diag;
+    }
+}
+
+template <class M, int H>
+__device__ __forceinline__ void region_load(const CaseParams& P, const MGLevel& lv, int x0, int y0, M* smu,
+                                            M* sr, M* se, unsigned char* in, bool load_e) {
+    using G = FRegion<H>;
+    const M* mu = static_cast<const M*>(lv.mu);
+    const M* r = static_cast<const M*>(lv.r);
+    const M* e = static_cast<const M*>(lv.e);
+    for (int k = threadIdx.x; k < G::N; k += blockDim.x) {
+        int gx, gy, sx, sy;
+        const int ok = region_source(P, lv.nx, lv.ny, x0, y0, H, G::W, k, gx, gy, sx, sy);
+        const size_t g = (size_t)sy * lv.pitch + sx;
+        in[k] = (unsigned char)ok;
+        smu[k] = ok ? mu[g] : M(0);
+        sr[k] = ok ? r[g] : M(0);
+        se[k] = (ok && load_e) ? e[g] : M(0);
+    }
+}
+
 template <class M>
-__global__ void __launch_bounds__(kNT) k_prolong(const DevCase* __restrict__ cases,
-                                                 const TileRef* __restrict__ tiles, int L) {
+__global__ void __launch_bounds__(256) k_vdown(const DevCase* __restrict__ cases,
+                                               const TileRef* __restrict__ tiles, int L) {
+    using G = FRegion<kHD>;
+    __shared__ M smu[G::N], sr[G::N], se[G::N];
+    __shared__ unsigned char in[G::N];
     const TileRef tr = tiles[blockIdx.x];
     const DevCase* dc = cases + tr.case_id;
     if (pot_done(dc) || L >= dc->nlev - 1) return;
     const CaseParams& P = dc->P;
-    const MGLevel f = dc->lev[L], c = dc->lev[L + 1];
-    const int i = tr.x0 + threadIdx.x % kMgTX, j = tr.y0 + threadIdx.x / kMgTX;
-    if (i >= f.nx || j >= f.ny) return;
-    const int I = i >> 1, J = j >> 1;
-    const int di = (i & 1) ? 1 : -1, dj = (j & 1) ? 1 : -1;
-    const M* ec = static_cast<const M*>(c.e);
-    const M v = M(9.0 / 16.0) * coarse_at<M>(P, ec, c.nx, c.ny, c.pitch, I, J) +
-                M(3.0 / 16.0) * coarse_at<M>(P, ec, c.nx, c.ny, c.pitch, I + di, J) +
-                M(3.0 / 16.0) * coarse_at<M>(P, ec, c.nx, c.ny, c.pitch, I, J + dj) +
-                M(1.0 / 16.0) * coarse_at<M>(P, ec, c.nx, c.ny, c.pitch, I + di, J + dj);
-    static_cast<M*>(f.e)[(size_t)j * f.pitch + i] += v;
+    const MGLevel lv = dc->lev[L], cv = dc->lev[L + 1];
+    region_load<M, kHD>(P, lv, tr.x0, tr.y0, smu, sr, se, in, false);
+    __syncthreads();
+    for (int h = 1; h <= 2 * kFNu; ++h) {
+        region_half_sweep<M, kHD>(P, lv.nx, lv.ny, tr.x0, tr.y0, smu, sr, se, in, (h - 1) & 1, h);
+        __syncthreads();
+    }
+    // pre-smoothed correction of the tile
+    M* e = static_cast<M*>(lv.e);
+    for (int t = threadIdx.x; t < kFTX * kFTY; t += blockDim.x) {
+        const int gx = tr.x0 + t % kFTX, gy = tr.y0 + t / kFTX;
+        if (gx < lv.nx && gy < lv.ny)
+            e[(size_t)gy * lv.pitch + gx] = se[(t / kFTX + kHD) * G::W + t % kFTX + kHD];
+    }
+    // restricted residual r - A e over the 2 x 2 children of each coarse cell
+    M* rc = static_cast<M*>(cv.r);
+    for (int t = threadIdx.x; t < (kFTX / 2) * (kFTY / 2); t += blockDim.x) {
+        const int ci = t % (kFTX / 2), cj = t / (kFTX / 2);
+        const int I = tr.x0 / 2 + ci, J = tr.y0 / 2 + cj;
+        if (I >= cv.nx || J >= cv.ny) continue;
+        M acc = 0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int lx = kHD + 2 * ci + (q & 1), ly = kHD + 2 * cj + (q >> 1);
+            const int k = ly * G::W + lx;
+            const int i = 2 * I + (q & 1), j = 2 * J + (q >> 1);
+            const M mc = smu[k], xc = se[k];
+            M ax = 0;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                int ii, jj;
+                if (neighbour(P, lv.nx, lv.ny, i, j, w, ii, jj)) {
+                    const int kn = k + (w == 0 ? -1 : w == 1 ? 1 : w == 2 ? -G::W : G::W);
+                    ax += M(0.5) * (mc + smu[kn]) * (xc - se[kn]);
+                } else if (P.mag_dir[w]) {
+                    ax += M(2) * mc * xc;
+                }
+            }
+            acc += sr[k] - ax;
+        }
+        rc[(size_t)J * cv.pitch + I] = acc;
+    }
+}
+
+template <class M>
+__global__ void __launch_bounds__(256) k_vup(const DevCase* __restrict__ cases,
+                                             const TileRef* __restrict__ tiles, int L) {
+    using G = FRegion<kHU>;
+    constexpr int CW = (kFTX + 2 * kHU) / 2 + 3, CH = (kFTY + 2 * kHU) / 2 + 3;
+    __shared__ M smu[G::N], sr[G::N], se[G::N];
+    __shared__ M sc[CW * CH];
+    __shared__ unsigned char in[G::N];
+    const TileRef tr = tiles[blockIdx.x];
+    const DevCase* dc = cases + tr.case_id;
+    if (pot_done(dc) || L >= dc->nlev - 1) return;
+    const CaseParams& P = dc->P;
+    const MGLevel lv = dc->lev[L], cv = dc->lev[L + 1];
+    region_load<M, kHU>(P, lv, tr.x0, tr.y0, smu, sr, se, in, true);
+    // coarse corrections around the region (one cell beyond its parents)
+    const int cx0 = (tr.x0 - kHU) / 2 - 1 - ((tr.x0 - kHU) < 0 ? 1 : 0);
+    const int cy0 = (tr.y0 - kHU) / 2 - 1 - ((tr.y0 - kHU) < 0 ? 1 : 0);
+    const M* ec = static_cast<const M*>(cv.e);
+    for (int k = threadIdx.x; k < CW * CH; k += blockDim.x) {
+        int I = cx0 + k % CW, J = cy0 + k / CW;
+        // periodic axes wrap; across a wall only the one-cell ghost is ever used by a
+        // cell inside the domain, so the rest is clamped onto it
+        if (P.periodic_x) I = ((I % cv.nx) + cv.nx) % cv.nx;
+        else I = I < -1 ? -1 : (I > cv.nx ? cv.nx : I);
+        if (P.periodic_y) J = ((J % cv.ny) + cv.ny) % cv.ny;
+        else J = J < -1 ? -1 : (J > cv.ny ? cv.ny : J);
+        sc[k] = coarse_at<M>(P, ec, cv.nx, cv.ny, cv.pitch, I, J);
+    }
+    __syncthreads();
+    for (int k = threadIdx.x; k < G::N; k += blockDim.x) {
+        if (!in[k]) continue;
+        const int gx = tr.x0 - kHU + k % G::W, gy = tr.y0 - kHU + k / G::W;
+        // parent of the region cell in unwrapped level coordinates
+        const int I = (gx >= 0 ? gx : gx - 1) / 2, J = (gy >= 0 ? gy : gy - 1) / 2;
+        const int di = (gx & 1) ? 1 : -1, dj = (gy & 1) ? 1 : -1;
+        const int a = (J - cy0) * CW + (I - cx0);
+        const M v = M(9.0 / 16.0) * sc[a] + M(3.0 / 16.0) * sc[a + di] + M(3.0 / 16.0) * sc[a + dj * CW] +
+                    M(1.0 / 16.0) * sc[a + di + dj * CW];
+        se[k] += v;
+    }
+    __syncthreads();
+    for (int h = 1; h <= 2 * kFNu; ++h) {
+        region_half_sweep<M, kHU>(P, lv.nx, lv.ny, tr.x0, tr.y0, smu, sr, se, in, (h - 1) & 1, h);
+        __syncthreads();
+    }
+    M* e = static_cast<M*>(lv.e);
+    for (int t = threadIdx.x; t < kFTX * kFTY; t += blockDim.x) {
+        const int gx = tr.x0 + t % kFTX, gy = tr.y0 + t / kFTX;
+        if (gx < lv.nx && gy < lv.ny)
+            e[(size_t)gy * lv.pitch + gx] = se[(t / kFTX + kHU) * G::W + t % kFTX + kHU];
+    }
 }
 
 // conjugate gradients on the coarsest level, one block per case, in shared memory
@@ -334,9 +506,17 @@ __global__ void __launch_bounds__(kNT) k_correct(const DevCase* __restrict__ cas
     const int i = tr.x0 + threadIdx.x % kMgTX, j = tr.y0 + threadIdx.x / kMgTX;
     if (i >= lv.nx || j >= lv.ny) return;
     const size_t k = (size_t)j * lv.pitch + i;
-    const double v = dc->phi64[k] + (double)static_cast<const M*>(lv.e)[k];
-    dc->phi64[k] = v;
-    static_cast<M*>(dc->phi)[k] = M(v);
+    if (sizeof(M) == 8) {
+        const double v = dc->phi64[k] + (double)static_cast<const M*>(lv.e)[k];
+        dc->phi64[k] = v;
+    } else {
+        // (phi, phi_lo) += e as a renormalised FP32 pair
+        float* hi = static_cast<float*>(dc->phi);
+        float h = hi[k], l = dc->phi_lo[k];
+        pair_add(h, l, (float)static_cast<const M*>(lv.e)[k], 0.f);
+        hi[k] = h;
+        dc->phi_lo[k] = l;
+    }
 }
 
 }  // namespace
@@ -364,27 +544,18 @@ cudaError_t launch_mg_finalize(const DevCase* cases, const int* ids, int ncases,
     return cudaGetLastError();
 }
 
-cudaError_t launch_mg_smooth(int prec, const DevCase* cases, const TileRef* tiles, int n, int L,
-                             int color, cudaStream_t st) {
+cudaError_t launch_mg_vdown(int prec, const DevCase* cases, const TileRef* tiles, int n, int L,
+                            cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    if (prec == 0) k_smooth<double><<<n, kNT, 0, st>>>(cases, tiles, L, color);
-    else k_smooth<float><<<n, kNT, 0, st>>>(cases, tiles, L, color);
+    if (prec == 0) k_vdown<double><<<n, 256, 0, st>>>(cases, tiles, L);
+    else k_vdown<float><<<n, 256, 0, st>>>(cases, tiles, L);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mg_restrict_resid(int prec, const DevCase* cases, const TileRef* tiles, int n,
-                                     int L, cudaStream_t st) {
+cudaError_t launch_mg_vup(int prec, const DevCase* cases, const TileRef* tiles, int n, int L, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    if (prec == 0) k_restrict_resid<double><<<n, kNT, 0, st>>>(cases, tiles, L);
-    else k_restrict_resid<float><<<n, kNT, 0, st>>>(cases, tiles, L);
-    return cudaGetLastError();
-}
-
-cudaError_t launch_mg_prolong(int prec, const DevCase* cases, const TileRef* tiles, int n, int L,
-                              cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    if (prec == 0) k_prolong<double><<<n, kNT, 0, st>>>(cases, tiles, L);
-    else k_prolong<float><<<n, kNT, 0, st>>>(cases, tiles, L);
+    if (prec == 0) k_vup<double><<<n, 256, 0, st>>>(cases, tiles, L);
+    else k_vup<float><<<n, 256, 0, st>>>(cases, tiles, L);
     return cudaGetLastError();
 }
 

@@ -359,7 +359,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
     const R c3 = R(1.0 / 3.0);
     const double b_rk = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
     const R dt = Q.dt;
-    double acc[kRedN] = {0, 0, 0, 0, 0, 0};
+    // step-end sums of this thread's cells: FP64 for C, H_e and F_l, counts as integers
+    double aC = 0.0, aH = 0.0, aF = 0.0;
+    int nDrop = 0, nBad = 0;
     HR* oHe = static_cast<HR*>(dc->He[out]);
     R* oP = static_cast<R*>(dc->p[out]);
     R* oMx = static_cast<R*>(dc->mx[out]);
@@ -445,16 +447,15 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
             const R Fsn = R(1) - Fln;
             R* mu0 = static_cast<R*>(dc->lev[0].mu);
             mu0[(size_t)gy * dc->lev[0].pitch + gx] = R(1) + mix(Fsn, Cn, Q.chi_s, Q.chi_l, Q.chi_g);
-            acc[0] += (double)Cn;
-            acc[1] += (double)Hen;
+            aC += (double)Cn;
+            aH += (double)Hen;
             if (Cn >= R(0.5)) {
-                acc[2] += (double)Fln;
-                acc[3] += 1.0;
-                acc[4] += (double)Fsn;
+                aF += (double)Fln;
+                nDrop += 1;
             }
             const bool fin = isfinite((double)Hen) && isfinite(pn) && isfinite(mxn) && isfinite(myn) &&
                              isfinite(Cn);
-            if (!fin) acc[5] += 1.0;
+            if (!fin) nBad += 1;
         }
         oHe[gi] = Hen;
         oP[gi] = pn;
@@ -463,19 +464,33 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         oC[gi] = Cn;
     }
     if (stage == 2) {
-        // block reduction of the diagnostics (FP64, fixed order)
+        // block reduction of the diagnostics (FP64 sums and integer counts, fixed
+        // order); the droplet's solid sum is its cell count minus its liquid sum
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-        for (int q = 0; q < kRedN; ++q) {
-            double v = acc[q];
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-            if (lane == 0) red_s[wid][q] = v;
+        for (int o = 16; o > 0; o >>= 1) {
+            aC += __shfl_down_sync(0xffffffffu, aC, o);
+            aH += __shfl_down_sync(0xffffffffu, aH, o);
+            aF += __shfl_down_sync(0xffffffffu, aF, o);
+            nDrop += __shfl_down_sync(0xffffffffu, nDrop, o);
+            nBad += __shfl_down_sync(0xffffffffu, nBad, o);
+        }
+        if (lane == 0) {
+            red_s[wid][0] = aC;
+            red_s[wid][1] = aH;
+            red_s[wid][2] = aF;
+            red_s[wid][3] = (double)nDrop;
+            red_s[wid][5] = (double)nBad;
         }
         __syncthreads();
-        if (threadIdx.x < kRedN) {
+        if (threadIdx.x < kRedN && threadIdx.x != 4) {
             double v = 0.0;
             for (int w = 0; w < NT / 32; ++w) v += red_s[w][threadIdx.x];
             dc->red[(size_t)tr.slot * kRedN + threadIdx.x] = v;
+            if (threadIdx.x == 2) {
+                double n = 0.0;
+                for (int w = 0; w < NT / 32; ++w) n += red_s[w][3];
+                dc->red[(size_t)tr.slot * kRedN + 4] = n - v;
+            }
         }
     }
 }
