@@ -65,6 +65,7 @@ class OracleStats(ct.Structure):
 
 FLAG_LITERAL_FSTAR_SIGN = 1
 FLAG_LITERAL_MUC_SIGN = 2
+FLAG_KEEP_POTENTIAL = 4
 
 _lib = None
 

@@ -676,8 +676,10 @@ static void step_once(oracle_state* s, int* status)
         s->Sdot[k] = (Fs - s->Fs_prev[k]) / dt;
         s->Fs_prev[k] = Fs; /* becomes F_s^{n} for the next step */
     }
-    int st = oracle_solve_potential(s);
-    if (st && !*status) *status = st;
+    if (!(c->flags & ORACLE_FLAG_KEEP_POTENTIAL)) {
+        int st = oracle_solve_potential(s);
+        if (st && !*status) *status = st;
+    }
     compute_H2(s);
     for (int n = 0; n < W_N; ++n) memcpy(s->w0 + n * N, s->W[n], N * sizeof(double));
     double* W0[W_N];

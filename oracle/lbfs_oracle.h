@@ -56,6 +56,9 @@ typedef struct oracle_case {
  * They exist so that tests can show that a pin catches the literal form. */
 #define ORACLE_FLAG_LITERAL_FSTAR_SIGN  1  /* Eq. 32 with "-" instead of "+"    */
 #define ORACLE_FLAG_LITERAL_MUC_SIGN    2  /* mu_c with "+kappa lap C"          */
+/* Keep the potential that was set instead of solving it at the start of a step: lets
+ * a test advance a window of a larger grid with that grid's solved potential. */
+#define ORACLE_FLAG_KEEP_POTENTIAL      4
 
 /* Field identifiers (same numbering as the library's field mask bits). */
 enum { OF_PHI = 0, OF_HE, OF_T, OF_FL, OF_P, OF_U, OF_V, OF_C, OF_MUC, OF_RHO,

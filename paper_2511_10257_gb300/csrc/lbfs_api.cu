@@ -353,8 +353,6 @@ lbfs_status potential_solve(lbfs_ctx* ctx) {
     if (ctx->n_pot == 0) return LBFS_OK;
     const int p = ctx->prec;
     cudaStream_t s = ctx->stream;
-    for (int L = 1; L < ctx->max_depth; ++L)
-        LK(launch_mg_restrict_mu(p, ctx->d_cases, ctx->d_mg_tiles[L], ctx->n_mg_tiles[L], L, s));
     const double no_fail = 1e300;
     if (p != 0 && !ctx->pot_fresh) {
         LK(launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], s));

@@ -121,6 +121,17 @@ __device__ __forceinline__ void invert_enthalpy(const CaseParams& P, HR He, R C,
     }
 }
 
+// a / b: exact in FP64; in FP32 the fast reciprocal-multiply (within 2 ulp), which
+// is below the rounding of the FP32 fluxes it feeds
+template <class R>
+__device__ __forceinline__ R fdiv(R a, R b) {
+    return a / b;
+}
+template <>
+__device__ __forceinline__ float fdiv<float>(float a, float b) {
+    return __fdividef(a, b);
+}
+
 template <class R>
 __device__ __forceinline__ R mix(R Fs, R C, R gs, R gl, R gg) {
     const R liq = gg + C * (gl - gg);
@@ -131,22 +142,25 @@ __device__ __forceinline__ R mix(R Fs, R C, R gs, R gl, R gg) {
 // in the enthalpy's precision H (FP64 storage in both modes) and everything after
 // them in R.  Hes_h = C_p,s T_m and L_h = L are given in H.
 template <class R, class H>
-__device__ __forceinline__ void invert_h(const PhysT<R>& Q, H Hes_h, H L_h, H He, R C, R& T, R& Fl) {
+__device__ __forceinline__ void invert_h(const PhysT<R>& Q, H Hes_h, H L_h, H He, R C, R& T, R& Fl,
+                                         R* He_r = nullptr) {
     const R cpL = Q.cp_g + C * (Q.cp_l - Q.cp_g);
-    const H Hel = Q.T_m == R(0) ? L_h : L_h + H(cpL * Q.T_m);
-    const R ds = R(He - Hes_h), dl = R(He - Hel);
+    const bool tm0 = Q.T_m == R(0);   // then H_es = 0 and H_el = L
+    const H Hel = tm0 ? L_h : L_h + H(cpL * Q.T_m);
+    const R ds = tm0 ? R(He) : R(He - Hes_h), dl = R(He - Hel);
+    if (He_r) *He_r = tm0 ? ds : ds + R(Hes_h);   // H_e in R for the reconstruction
     if (C < R(0.5)) {
         Fl = R(1);
-        T = Q.T_m + dl / cpL;
+        T = Q.T_m + fdiv(dl, cpL);
     } else if (ds < R(0)) {
         Fl = R(0);
-        T = Q.T_m + ds / Q.cp_s;
+        T = Q.T_m + fdiv(ds, Q.cp_s);
     } else if (dl <= R(0)) {
-        Fl = ds / (ds - dl);
+        Fl = fdiv(ds, ds - dl);
         T = Q.T_m;
     } else {
         Fl = R(1);
-        T = Q.T_m + dl / cpL;
+        T = Q.T_m + fdiv(dl, cpL);
     }
 }
 

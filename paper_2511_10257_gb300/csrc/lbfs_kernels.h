@@ -19,8 +19,6 @@ cudaError_t launch_stage(int prec, int tile, int half, const DevCase* cases, con
 
 // potential multigrid (lbfs_potential.cu).  MG tiles are 32 x 8 cells of one level.
 constexpr int kMgTX = 32, kMgTY = 8;
-cudaError_t launch_mg_restrict_mu(int prec, const DevCase* cases, const TileRef* tiles, int n,
-                                  int level_coarse, cudaStream_t st);
 cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* tiles, int n,
                                  cudaStream_t st);
 // tol: the convergence test; a residual above fail_tol marks the case's solve failed

@@ -73,22 +73,8 @@ __device__ __forceinline__ M apply_A(const CaseParams& P, const M* mu, const M* 
     return acc;
 }
 
-template <class M>
-__global__ void __launch_bounds__(kNT) k_restrict_mu(const DevCase* __restrict__ cases,
-                                                     const TileRef* __restrict__ tiles, int L) {
-    const TileRef tr = tiles[blockIdx.x];
-    const DevCase* dc = cases + tr.case_id;
-    const MGLevel c = dc->lev[L], f = dc->lev[L - 1];
-    const int I = tr.x0 + threadIdx.x % kMgTX, J = tr.y0 + threadIdx.x / kMgTX;
-    if (I >= c.nx || J >= c.ny) return;
-    const M* mf = static_cast<const M*>(f.mu);
-    const size_t k0 = (size_t)(2 * J) * f.pitch + 2 * I;
-    static_cast<M*>(c.mu)[(size_t)J * c.pitch + I] =
-        M(0.25) * ((mf[k0] + mf[k0 + 1]) + (mf[k0 + f.pitch] + mf[k0 + f.pitch + 1]));
-}
-
-// FP64-accurate residual of the master potential on the fine level, zeroes the
-// correction, and per-tile partial sums of |r|^2 and |b|^2.
+// FP64-accurate residual of the master potential on the fine level and per-tile
+// partial sums of |r|^2 and |b|^2.
 //   r = b - A phi = -[sum_nb mu_f (phi_c - phi_nb) + sum_Dirichlet 2 mu_c (phi_c - phi_w)]
 // FP64 mode: in FP64.  Mixed mode: the master potential is the FP32 pair phi + phi_lo
 // and the differences, products and sums are error-free pair operations on the FP32
@@ -179,7 +165,6 @@ __global__ void __launch_bounds__(kNT) k_residual64(const DevCase* __restrict__ 
         const double r = residual_cell<M>(dc, P, lv, i, j, b);
         const size_t k = (size_t)j * lv.pitch + i;
         static_cast<M*>(lv.r)[k] = M(r);
-        static_cast<M*>(lv.e)[k] = M(0);
         if (sizeof(M) == 8) {
             r2 = r * r;
         } else {
@@ -356,13 +341,20 @@ __global__ void __launch_bounds__(256) k_vdown(const DevCase* __restrict__ cases
         if (gx < lv.nx && gy < lv.ny)
             e[(size_t)gy * lv.pitch + gx] = se[(t / kFTX + kHD) * G::W + t % kFTX + kHD];
     }
-    // restricted residual r - A e over the 2 x 2 children of each coarse cell
+    // restricted residual r - A e over the 2 x 2 children of each coarse cell, and
+    // the coarse coefficient as the mean of the children's
     M* rc = static_cast<M*>(cv.r);
+    M* muc = static_cast<M*>(cv.mu);
     for (int t = threadIdx.x; t < (kFTX / 2) * (kFTY / 2); t += blockDim.x) {
         const int ci = t % (kFTX / 2), cj = t / (kFTX / 2);
         const int I = tr.x0 / 2 + ci, J = tr.y0 / 2 + cj;
         if (I >= cv.nx || J >= cv.ny) continue;
         M acc = 0;
+        {
+            const int k0 = (kHD + 2 * cj) * G::W + kHD + 2 * ci;
+            muc[(size_t)J * cv.pitch + I] =
+                M(0.25) * ((smu[k0] + smu[k0 + 1]) + (smu[k0 + G::W] + smu[k0 + G::W + 1]));
+        }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int lx = kHD + 2 * ci + (q & 1), ly = kHD + 2 * cj + (q >> 1);
@@ -520,14 +512,6 @@ __global__ void __launch_bounds__(kNT) k_correct(const DevCase* __restrict__ cas
 }
 
 }  // namespace
-
-cudaError_t launch_mg_restrict_mu(int prec, const DevCase* cases, const TileRef* tiles, int n, int L,
-                                  cudaStream_t st) {
-    if (n <= 0) return cudaSuccess;
-    if (prec == 0) k_restrict_mu<double><<<n, kNT, 0, st>>>(cases, tiles, L);
-    else k_restrict_mu<float><<<n, kNT, 0, st>>>(cases, tiles, L);
-    return cudaGetLastError();
-}
 
 cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* tiles, int n,
                                  cudaStream_t st) {

@@ -127,7 +127,7 @@ __device__ __forceinline__ void face_flux(const PhysT<R>& Q, const R* __restrict
     // Eq. 45: interface values
     const R Cf = SC_, pf = Sp, Hef = SH;
     const R rhof = mix(Fsm, Cf, rs, rl, rg);
-    const R inv_rc = R(3) / rhof;                 // 1 / (rho_f c_s^2)
+    const R inv_rc = fdiv(R(3), rhof);                 // 1 / (rho_f c_s^2)
     const R ufn = Sjn * inv_rc, uft = Sjt * inv_rc;
     const R cpf = mix(Fsm, Cf, cs, cl, cg);
     const R lamf = mix(Fsm, Cf, Q.lam_s, Q.lam_l, Q.lam_g);
@@ -169,7 +169,7 @@ __device__ __forceinline__ void wall_flux(const PhysT<R>& Q, int dirichlet, cons
         F[3] = c3 * s[SP * RN + k];
         F[2] = c3 * (-mu * dut);
     }
-    F[0] = dirichlet ? -(lam / rho) * dT : R(0);
+    F[0] = dirichlet ? -fdiv(lam, rho) * dT : R(0);
 }
 
 template <class R, class HR, int TX, int TY, int NT, int MINB, bool HALF>
@@ -257,13 +257,13 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         const HR He = gHe[gi];
         const R C = gC[gi];
         R T, Fl;
-        invert_h<R, HR>(Q, Hes_h, L_h, He, C, T, Fl);
+        R Hes;   // H_e for the reconstruction (enters only the interface T_f)
+        invert_h<R, HR>(Q, Hes_h, L_h, He, C, T, Fl, &Hes);
         const R Fs = R(1) - Fl;
         const R rho = mix(Fs, C, Q.rho_s, Q.rho_l, Q.rho_g);
-        const R rinv = R(3) / rho;
+        const R rinv = fdiv(R(3), rho);
         R u = gMx[gi] * rinv, v = gMy[gi] * rinv;
         R phi = gPhi[gi];
-        R Hes = R(He);   // H_e for the reconstruction (enters only the interface T_f)
         if (wall >= 0) {
             u = -u;
             v = -v;
