@@ -93,9 +93,10 @@ def stage_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(tile_name: str, grid: str):
-    """DRAM bytes per stage launch from the committed ncu summary of this kernel
-    version, tile shape and grid (None when the kernel changed since the capture)"""
+def profiled(tile_name: str, grid: str, key: str):
+    """a per-launch counter of the stage kernel from the committed ncu summary of this
+    kernel version, tile shape and grid (None when the kernel changed since the
+    capture): dram_bytes_per_launch_avg or warp_inst_per_launch"""
     path = os.path.join(ROOT, "profiles", "stage_kernel_4096x2048.md")
     try:
         kv = {}
@@ -105,7 +106,7 @@ def profiled_traffic(tile_name: str, grid: str):
                 kv[k.strip()] = v.strip().strip("`")
         if (kv.get("source_sha256") == stage_source_hash() and kv.get("tile") == tile_name
                 and kv.get("grid") == grid):
-            return float(kv["dram_bytes_per_launch_avg"])
+            return float(kv[key])
     except Exception:
         return None
     return None
@@ -230,7 +231,7 @@ def run_gpu(args):
     prec = lbfs.FP64 if args.precision == "fp64" else lbfs.MIXED
     stream = torch.cuda.current_stream()
     solver = lbfs.Solver(precision=prec, max_cases=len(cases), device=local, stream=stream.cuda_stream,
-                         torch_alloc=True, tile=max(args.tile, 0), use_graph=args.graph)
+                         torch_alloc=True, tile=max(args.tile, 0), use_graph=True)
     for k, c in enumerate(cases):
         solver.set_case(k, c)
     ncell = sum(c["nx"] * c["ny"] for c in cases)
@@ -250,7 +251,8 @@ def run_gpu(args):
     barrier()
     clocks = ClockSampler(local)
     clocks.start()
-    solver.timing(True)
+    # per-kernel events run eagerly; --graph 1 times graph replay without them
+    solver.timing(not args.graph)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     ev0.record(stream)
@@ -269,31 +271,32 @@ def run_gpu(args):
     # pinned host memory, K steps each returning its statistics, download C, F_l, T
     e2e = None
     if not args.no_e2e:
-        in_ids = [I.HE, I.P, I.C, I.MX, I.MY, I.FSPREV, I.PHI]
-        out_ids = [I.C, I.FL, I.T]
-        hosts = []
+        in_ids = sorted([I.HE, I.P, I.C, I.MX, I.MY, I.FSPREV, I.PHI])
+        out_ids = sorted([I.C, I.FL, I.T])
+        hosts, outs = [], []
         for k, c in enumerate(cases):
-            state = solver.fields(k, in_ids)
-            pinned = torch.empty((len(in_ids), c["ny"], c["nx"]), dtype=torch.float64, pin_memory=True)
-            host = pinned.numpy()
-            for q, f in enumerate(in_ids):
-                host[q] = state[f]
+            host = torch.empty((len(in_ids), c["ny"], c["nx"]), dtype=torch.float64, pin_memory=True).numpy()
+            solver.fields_into(k, in_ids, host)
             hosts.append(host)
+            outs.append(torch.empty((len(out_ids), c["ny"], c["nx"]), dtype=torch.float64,
+                                    pin_memory=True).numpy())
         stats_bytes = 80 * len(cases)
         barrier()
         t0 = time.perf_counter()
         for k, host in enumerate(hosts):
-            solver.set_fields(k, {f: host[q] for q, f in enumerate(in_ids)})
+            solver.set_fields_packed(k, in_ids, host)
         for _ in range(args.steps):
             solver.step(1)
         for k in range(len(cases)):
-            solver.fields(k, out_ids)
+            solver.fields_into(k, out_ids, outs[k])
         barrier()
         t_e2e = time.perf_counter() - t0
         t_e2e, units_e2e = reduce_over_ranks(t_e2e, ncell * args.steps, world)
         e2e = {"value": units_e2e / t_e2e / 1e6, "unit": UNIT,
                "h2d_bytes_per_step": int(len(in_ids) * 8 * ncell / args.steps),
-               "d2h_bytes_per_step": int(stats_bytes + len(out_ids) * 8 * ncell / args.steps)}
+               "d2h_bytes_per_step": int(stats_bytes + len(out_ids) * 8 * ncell / args.steps),
+               "job": "upload the state from pinned host memory, step by step with the statistics "
+                      "returned each step, download C, F_l and T"}
 
     # plain FP64 path on the same grid for the mixed-versus-FP64 speed-up
     fp64 = None
@@ -319,13 +322,24 @@ def run_gpu(args):
         return 0
     peak, peak_kind = measured_peak()
     bpc = stage_bytes_per_cell(prec)
-    stage_avg_s = st_ms / max(st_n, 1) / 1e3
+    stage_avg_s = st_ms / max(st_n, 1) / 1e3 if st_n else float("nan")
     achieved = ncell * bpc / stage_avg_s / 1e9
-    traffic = profiled_traffic(lbfs.TILE_NAMES[tile], f"{case['nx']}x{case['ny']}") if len(cases) == 1 else None
+    gname = f"{case['nx']}x{case['ny']}"
+    traffic = profiled(lbfs.TILE_NAMES[tile], gname, "dram_bytes_per_launch_avg") if len(cases) == 1 else None
+    winst = profiled(lbfs.TILE_NAMES[tile], gname, "warp_inst_per_launch") if len(cases) == 1 else None
+    # issue roofline: 152 SMs x 4 schedulers issue one warp instruction per clock each
+    sm_mhz = clk.get("sm_mhz") or 2070.0
+    issue_peak = 152 * 4 * sm_mhz * 1e6
+    issue = None
+    if winst is not None:
+        issue = {"achieved_warp_inst_per_s": winst / stage_avg_s, "peak_warp_inst_per_s": issue_peak,
+                 "frac": winst / stage_avg_s / issue_peak,
+                 "note": "executed instructions per launch from the committed ncu capture"}
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": "stage_kernel",
                 "peak_source": peak_kind, "bytes_per_cell": bpc,
-                "launch_ms": stage_avg_s * 1e3, "potential_ms_per_step": pot_ms / max(pot_n, 1),
+                "launch_ms": stage_avg_s * 1e3, "issue": issue,
+                "potential_ms_per_step": pot_ms / max(pot_n, 1),
                 "finalize_ms_per_step": fin_ms / max(fin_n, 1)}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
@@ -346,7 +360,10 @@ def run_gpu(args):
         "dtype": "f64" if prec == lbfs.FP64 else "f32+f64",
         "data": "synthetic",
         "config": {"workload": name, "grid": grid, "cases": len(cases),
-                   "precision": args.precision, "graph": bool(args.graph),
+                   "precision": args.precision,
+                   "execution": ("timed steps replay the recorded CUDA graph" if args.graph else
+                                 "timed steps launch eagerly with per-kernel CUDA events; the e2e job "
+                                 "replays the recorded CUDA graph"),
                    "tile": lbfs.TILE_NAMES[tile],
                    "autotune_ms_per_shape": {nm: round(m, 4) for nm, m in zip(lbfs.TILE_NAMES, tile_ms)},
                    "l2": f"inputs larger than L2: per-step working set {3 * state_bytes / 2**20:.0f} MiB "

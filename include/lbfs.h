@@ -155,6 +155,27 @@ lbfs_status lbfs_step(lbfs_ctx* ctx, int32_t nsteps, lbfs_case_stats* out);
 /* Copy fields of a case to caller-owned host memory (FP64, see field ids). */
 lbfs_status lbfs_fields(lbfs_ctx* ctx, int32_t case_id, uint32_t mask, double* host_out);
 
+/* Sec. 5 diagnostics of a case's current state (lattice units, FP64 arithmetic). */
+typedef struct lbfs_case_diag {
+    double H_m;      /* droplet height (Sec. 5.1): the highest point where C crosses 1/2 in
+                        any column, linear in y between cell centres; 0 without droplet   */
+    double U_max;    /* largest speed |u| over the droplet cells (C >= 1/2)               */
+    double Pe;       /* Peclet number U_max D / alpha_l, D = 2 R_0, alpha_l = lambda_l /
+                        (rho_l C_p,l) (Eq. 50, its garbled "D u^2/alpha" read as U D/alpha) */
+    double Fo;       /* Fourier number lambda_l t / (rho_l C_p,l R_0^2) (Eq. 50)          */
+    double Q_wall;   /* sum over the bottom-wall faces of the local heat flux Q dx        */
+} lbfs_case_diag;
+
+/* Diagnostics of case case_id (Sec. 5.1-5.2) computed on the device from the stored
+ * state, on the context's stream, waiting for completion.  R_0 is the case's radius.
+ * The local heat flux on the cold substrate is Q = -lambda dT/dy at y = 0, the slope
+ * being the second-order one-sided difference (-8 T_w + 9 T_0 - T_1)/3 through the
+ * wall temperature and the first two cell centres, lambda the first cell's Eq. 11
+ * value; Q = 0 where the bottom wall is adiabatic or the y axis periodic.
+ * out: caller-owned, one struct.  q_wall: caller-owned host array of nx doubles that
+ * receives Q per column, or NULL.  LBFS_EINVAL for an undefined case or a NULL out. */
+lbfs_status lbfs_diagnostics(lbfs_ctx* ctx, int32_t case_id, lbfs_case_diag* out, double* q_wall);
+
 /* Number of device kernel launches the last lbfs_step issued (graph nodes count). */
 int64_t lbfs_last_launch_count(const lbfs_ctx* ctx);
 
@@ -162,10 +183,12 @@ int64_t lbfs_last_launch_count(const lbfs_ctx* ctx);
  * grid; the halo is fixed at three cells by the stencil).  Times `reps` launches of
  * each compiled tile shape on the context's current cases (Runge-Kutta stage 2,
  * which writes only a stage buffer, so the state is untouched), keeps the fastest
+ * (a shape with a higher id must be more than 2 % faster than the best before it)
  * for later steps and writes its id to *chosen (nullable).  ms (nullable, n entries)
  * receives the milliseconds per launch of each shape id < n.  Shapes: 0 32x8,
  * 1 32x16, 2 64x8, 3 16x16, 4 64x4, 5 16x16 and 6 32x8 with registers cut for a
- * third resident block per SM (mixed precision). */
+ * third resident block per SM (mixed precision), 7 and 8: shapes 5 and 6 launched
+ * persistently (a grid of resident blocks striding over the tile list of all cases). */
 lbfs_status lbfs_autotune(lbfs_ctx* ctx, int32_t reps, int32_t* chosen, double* ms, int32_t n);
 
 /* Kernel timing.  While enabled, lbfs_step brackets every launch with CUDA events on

@@ -63,6 +63,11 @@ class OracleStats(ct.Structure):
                 ("pot_iters", ct.c_int32), ("nonfinite", ct.c_int32)]
 
 
+class OracleDiag(ct.Structure):
+    _fields_ = [("H_m", ct.c_double), ("U_max", ct.c_double), ("Pe", ct.c_double),
+                ("Fo", ct.c_double), ("Q_wall", ct.c_double)]
+
+
 FLAG_LITERAL_FSTAR_SIGN = 1
 FLAG_LITERAL_MUC_SIGN = 2
 FLAG_KEEP_POTENTIAL = 4
@@ -93,6 +98,7 @@ def lib():
         L.oracle_solve_potential.argtypes = [ct.c_void_p]
         L.oracle_pseudo_time_potential.argtypes = [ct.c_void_p, ct.c_int32, ct.c_double]
         L.oracle_rhs.argtypes = [ct.c_void_p, pd]
+        L.oracle_diagnostics.argtypes = [ct.c_void_p, ct.POINTER(OracleDiag), pd]
     return _lib
 
 
@@ -165,6 +171,13 @@ class Oracle:
         s = OracleStats()
         lib().oracle_get_stats(self._h, ct.byref(s))
         return {n: getattr(s, n) for n, _ in OracleStats._fields_}
+
+    def diagnostics(self):
+        """(dict of H_m, U_max, Pe, Fo, Q_wall; local wall heat flux Q per column)"""
+        d = OracleDiag()
+        q = np.zeros(self.nx)
+        lib().oracle_diagnostics(self._h, ct.byref(d), _ptr(q))
+        return {n: getattr(d, n) for n, _ in OracleDiag._fields_}, q
 
     def face_flux(self, axis: int, i: int, j: int) -> np.ndarray:
         out = np.zeros(5)

@@ -898,6 +898,85 @@ int oracle_set_field(oracle_state* s, int32_t field, const double* in)
     return 0;
 }
 
+/* ---- Sec. 5 diagnostics --------------------------------------------------------
+ * Local heat flux on the cold substrate (Sec. 5.2): Q = -lambda dT/dy at y = 0, the
+ * gradient by a second-order one-sided difference.  The quadratic through the wall
+ * value T_w (y = 0) and the first two cell centres (y = 1/2, 3/2) has the slope
+ * (-8 T_w + 9 T_0 - T_1)/3 at the wall; with a single row the two-point slope
+ * (T_0 - T_w)/(1/2) is used.  lambda is the first cell's Eq. 11 value.  An adiabatic
+ * bottom wall has Q = 0, and a periodic y axis has no wall (Q = 0).
+ * Droplet height H_m (Sec. 5.1, Fig. 11): in each column the highest point where C
+ * crosses 1/2, linear in y between the cell centres on either side (ny when the top
+ * cell has C >= 1/2); H_m is the largest over the columns, 0 without droplet cells.
+ * Peclet number (Eq. 50, printed garbled as D u^2/alpha): read as U D / alpha_l with
+ * U the largest speed |u| over the droplet cells (C >= 1/2), D = 2 R_0 and
+ * alpha_l = lambda_l/(rho_l C_p,l).  Fourier number (Eq. 50): lambda_l t/(rho_l C_p,l R_0^2).
+ * ------------------------------------------------------------------------------ */
+int oracle_diagnostics(oracle_state* s, oracle_diag* out, double* q_wall)
+{
+    const oracle_case* c = &s->cs;
+    const int nx = s->nx, ny = s->ny;
+    const int wall = !c->periodic_y && c->thermal_dirichlet[2];
+    double Hm = 0.0, Umax = 0.0, Qsum = 0.0;
+    for (int i = 0; i < nx; ++i) {
+        /* height: scan down from the top for the first droplet cell */
+        for (int j = ny - 1; j >= 0; --j) {
+            double C = s->W[W_C][CI(s, i, j)];
+            if (C >= 0.5) {
+                double h;
+                if (j == ny - 1) {
+                    h = (double)ny;
+                } else {
+                    double Cu = s->W[W_C][CI(s, i, j + 1)];
+                    h = (j + 0.5) + (C - 0.5) / (C - Cu);
+                }
+                if (h > Hm) Hm = h;
+                break;
+            }
+        }
+        /* largest speed over the column's droplet cells */
+        for (int j = 0; j < ny; ++j) {
+            size_t k = CI(s, i, j);
+            double C = s->W[W_C][k];
+            if (C < 0.5) continue;
+            double T, Fl;
+            oracle_eq8(c, s->W[W_HE][k], C, &T, &Fl);
+            double rho = oracle_mix(1.0 - Fl, C, c->rho_s, c->rho_l, c->rho_g);
+            double u = s->W[W_MX][k] / (rho * CS2), v = s->W[W_MY][k] / (rho * CS2);
+            double sp = sqrt(u * u + v * v);
+            if (sp > Umax) Umax = sp;
+        }
+        /* wall heat flux of this column */
+        double Q = 0.0;
+        if (wall) {
+            double T0, Fl0;
+            size_t k0 = CI(s, i, 0);
+            oracle_eq8(c, s->W[W_HE][k0], s->W[W_C][k0], &T0, &Fl0);
+            double lam = oracle_mix(1.0 - Fl0, s->W[W_C][k0], c->lam_s, c->lam_l, c->lam_g);
+            double Tw = c->wall_T[2], dTdy;
+            if (ny >= 2) {
+                double T1, Fl1;
+                size_t k1 = CI(s, i, 1);
+                oracle_eq8(c, s->W[W_HE][k1], s->W[W_C][k1], &T1, &Fl1);
+                dTdy = (-8.0 * Tw + 9.0 * T0 - T1) / 3.0;
+            } else {
+                dTdy = (T0 - Tw) / 0.5;
+            }
+            Q = -lam * dTdy;
+        }
+        if (q_wall) q_wall[i] = Q;
+        Qsum += Q;
+    }
+    const double R0 = c->radius;
+    const double alpha_l = c->lam_l / (c->rho_l * c->cp_l);
+    out->H_m = Hm;
+    out->U_max = Umax;
+    out->Pe = Umax * 2.0 * R0 / alpha_l;
+    out->Fo = c->lam_l * s->t / (c->rho_l * c->cp_l * R0 * R0);
+    out->Q_wall = Qsum;
+    return 0;
+}
+
 /* ---- pieces for pin tests ---------------------------------------------------- */
 
 /* flux of one face of the current state; Sdot and |H|^2 are not used by fluxes */

@@ -81,6 +81,16 @@ int  oracle_set_field(oracle_state* s, int32_t field, const double* in);
 void oracle_get_stats(oracle_state* s, oracle_stats* out);
 void oracle_set_threads(int32_t n);
 
+/* Sec. 5 diagnostics of the current state (see oracle_diagnostics). */
+typedef struct oracle_diag {
+    double H_m;        /* droplet height above the bottom wall                      */
+    double U_max;      /* largest speed over droplet cells (C >= 1/2)               */
+    double Pe;         /* U_max D / alpha_l, D = 2 R_0                              */
+    double Fo;         /* lambda_l t / (rho_l C_p,l R_0^2)                           */
+    double Q_wall;     /* sum over the bottom-wall faces of the local heat flux Q dx */
+} oracle_diag;
+int oracle_diagnostics(oracle_state* s, oracle_diag* out, double* q_wall /* nx or NULL */);
+
 /* Pieces exposed for pin tests. */
 void   oracle_eq8(const oracle_case* cs, double He, double C, double* T, double* Fl);
 double oracle_mix(double Fs, double C, double g_s, double g_l, double g_g);

@@ -241,6 +241,11 @@ void fill_phys(const CaseParams& P, PhysT<R>& q) {
     q.tau_g = R(0.5 + P.mobility / (P.Q_g * P.dts));
     q.dt = R(P.dt); q.vol_ratio = R(P.vol_ratio); q.gravity = R(P.gravity); q.T_m = R(P.T_m); q.L = R(P.L);
     for (int w = 0; w < 4; ++w) q.wall_T[w] = R(P.wall_T[w]);
+    const double Hes = P.cp_s * P.T_m;
+    q.Hes_hi = R(Hes);
+    q.Hes_lo = R(Hes - double(q.Hes_hi));
+    q.L_hi = R(P.L);
+    q.L_lo = R(P.L - double(q.L_hi));
 }
 
 // Upload the concatenated tile lists of all defined cases.
@@ -356,7 +361,7 @@ lbfs_status potential_solve(lbfs_ctx* ctx) {
     const double no_fail = 1e300;
     if (p != 0 && !ctx->pot_fresh) {
         LK(launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], s));
-        LK(launch_mg_finalize(ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, ctx->mg_tol * 1e4, 1,
+        LK(launch_mg_finalize(p, ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, ctx->mg_tol * 1e4, 1,
                               ctx->d_flag, s));
         lbfs_status r = vcycle(ctx);
         if (r != LBFS_OK) return r;
@@ -366,7 +371,7 @@ lbfs_status potential_solve(lbfs_ctx* ctx) {
     for (int it = 0;; ++it) {
         LK(launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], s));
         CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
-        LK(launch_mg_finalize(ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, no_fail, it == 0, ctx->d_flag, s));
+        LK(launch_mg_finalize(p, ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, no_fail, it == 0, ctx->d_flag, s));
         CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (*ctx->h_flag == 0) break;
@@ -394,7 +399,7 @@ lbfs_status one_step(lbfs_ctx* ctx) {
         toc(ctx, LBFS_TIMING_STAGE, t1);
     }
     cudaEvent_t t2 = tic(ctx);
-    LK(launch_step_finalize(ctx->d_cases, ctx->d_active, ctx->n_active, ctx->stream));
+    LK(launch_step_finalize(ctx->prec, ctx->d_cases, ctx->d_active, ctx->n_active, ctx->stream));
     toc(ctx, LBFS_TIMING_FINALIZE, t2);
     return LBFS_OK;
 }
@@ -638,6 +643,33 @@ lbfs_status lbfs_fields(lbfs_ctx* ctx, int32_t id, uint32_t mask, double* host_o
     return LBFS_OK;
 }
 
+lbfs_status lbfs_diagnostics(lbfs_ctx* ctx, int32_t id, lbfs_case_diag* out, double* q_wall) {
+    lbfs_status r = check_case(ctx, id);
+    if (r != LBFS_OK) return r;
+    Slot& s = ctx->slots[id];
+    if (!s.defined) return fail(ctx, LBFS_EINVAL, "case not defined");
+    if (!out) return fail(ctx, LBFS_EINVAL, "out is NULL");
+    CK(cudaSetDevice(ctx->cfg.device));
+    const int nx = s.hd.P.nx;
+    r = ensure_scratch(ctx, (3 * (size_t)nx + 5) * sizeof(double));
+    if (r != LBFS_OK) return r;
+    double* cols = ctx->d_scratch;
+    double* res = ctx->d_scratch + 3 * (size_t)nx;
+    CK(launch_diagnostics(ctx->prec, ctx->d_cases + id, nx, s.desc.radius, cols, res, ctx->stream));
+    double h[5];
+    CK(cudaMemcpyAsync(h, res, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    if (q_wall)
+        CK(cudaMemcpyAsync(q_wall, cols + 2 * (size_t)nx, nx * sizeof(double), cudaMemcpyDeviceToHost,
+                           ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    out->H_m = h[0];
+    out->U_max = h[1];
+    out->Pe = h[2];
+    out->Fo = h[3];
+    out->Q_wall = h[4];
+    return LBFS_OK;
+}
+
 lbfs_status lbfs_step(lbfs_ctx* ctx, int32_t nsteps, lbfs_case_stats* out) {
     if (!ctx) return LBFS_EINVAL;
     if (nsteps < 0) return fail(ctx, LBFS_EINVAL, "nsteps must be >= 0");
@@ -729,7 +761,9 @@ lbfs_status lbfs_autotune(lbfs_ctx* ctx, int32_t reps, int32_t* chosen, double* 
         CK(cudaEventElapsedTime(&el, a, b));
         const double per = el / reps;
         if (t < n && ms) ms[t] = per;
-        if (per < best_ms) {
+        // a later shape must be more than 2 % faster to replace the current choice, so
+        // near-ties resolve to the same shape from run to run
+        if (per < 0.98 * best_ms) {
             best_ms = per;
             best = t;
         }

@@ -31,7 +31,7 @@ __global__ void k_init(const DevCase* __restrict__ dc, InitArgs a) {
     const double cp = mixture<double>(0.0, C, P.cp_s, P.cp_l, P.cp_g);
     const double He = cp * a.T_init + P.L;
     const size_t k = (size_t)j * P.pitch + i;
-    static_cast<double*>(dc->He[0])[k] = He;
+    he_set<R>(dc->He[0], k, He);
     static_cast<R*>(dc->p[0])[k] = R(0);
     static_cast<R*>(dc->mx[0])[k] = R(0);
     static_cast<R*>(dc->my[0])[k] = R(0);
@@ -50,7 +50,7 @@ __global__ void k_mu_from_state(const DevCase* __restrict__ dc) {
     const size_t k = (size_t)j * P.pitch + i;
     const R C = static_cast<const R*>(dc->C[0])[k];
     R T, Fl;
-    invert_enthalpy<R, double>(P, static_cast<const double*>(dc->He[0])[k], C, T, Fl);
+    invert_enthalpy<R, double>(P, he_get<R>(dc->He[0], k), C, T, Fl);
     static_cast<R*>(dc->lev[0].mu)[(size_t)j * dc->lev[0].pitch + i] =
         R(1) + mixture(R(1) - Fl, C, P.chi_s, P.chi_l, P.chi_g);
 }
@@ -72,7 +72,7 @@ __global__ void k_derive(const DevCase* __restrict__ dc, uint32_t mask, double* 
     if (!cell_of(P.nx, P.ny, i, j)) return;
     const size_t k = (size_t)j * P.pitch + i;
     const size_t N = (size_t)P.nx * P.ny, o = (size_t)j * P.nx + i;
-    const double He = static_cast<const double*>(dc->He[0])[k];
+    const double He = he_get<R>(dc->He[0], k);
     const R* Cg = static_cast<const R*>(dc->C[0]);
     const R C = Cg[k];
     R T, Fl;
@@ -108,6 +108,106 @@ __global__ void k_derive(const DevCase* __restrict__ dc, uint32_t mask, double* 
     }
 }
 
+// Sec. 5 diagnostics, one thread per column (rows are read coalesced across the
+// threads of a block):
+//  - the column's droplet height: the highest point where C crosses 1/2, linear in y
+//    between the cell centres on either side, ny when the top cell has C >= 1/2;
+//  - the largest speed |u| over the column's droplet cells (C >= 1/2);
+//  - the local heat flux on a cold (Dirichlet) bottom wall, Q = -lambda dT/dy at y = 0
+//    (Sec. 5.2).  The slope is that of the quadratic through the wall value at y = 0 and
+//    the first two cell centres (y = 1/2, 3/2): (-8 T_w + 9 T_0 - T_1)/3; a single row
+//    uses (T_0 - T_w)/(1/2).  lambda is the first cell's Eq. 11 conductivity.
+// Everything is evaluated in FP64 from the stored state.  cols holds three rows of nx.
+template <class R>
+__global__ void k_diag_columns(const DevCase* __restrict__ dc, double* __restrict__ cols) {
+    const CaseParams& P = dc->P;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P.nx) return;
+    const R* Cg = static_cast<const R*>(dc->C[0]);
+    const R* mxg = static_cast<const R*>(dc->mx[0]);
+    const R* myg = static_cast<const R*>(dc->my[0]);
+    const void* Heg = dc->He[0];
+    double h = 0.0, umax = 0.0, C_above = 0.0;
+    bool top_found = false;
+    for (int j = P.ny - 1; j >= 0; --j) {
+        const size_t k = (size_t)j * P.pitch + i;
+        const double C = (double)Cg[k];
+        if (C >= 0.5) {
+            if (!top_found) {
+                top_found = true;
+                h = (j == P.ny - 1) ? (double)P.ny : (j + 0.5) + (C - 0.5) / (C - C_above);
+            }
+            double T, Fl;
+            invert_enthalpy<double, double>(P, he_get<R>(Heg, k), C, T, Fl);
+            const double rho = mixture<double>(1.0 - Fl, C, P.rho_s, P.rho_l, P.rho_g);
+            const double u = (double)mxg[k] * 3.0 / rho, v = (double)myg[k] * 3.0 / rho;
+            umax = fmax(umax, sqrt(u * u + v * v));
+        }
+        C_above = C;
+    }
+    double Q = 0.0;
+    if (!P.periodic_y && P.thermal_dir[2]) {
+        const double C0 = (double)Cg[i];
+        double T0, Fl0;
+        invert_enthalpy<double, double>(P, he_get<R>(Heg, i), C0, T0, Fl0);
+        const double lam = mixture<double>(1.0 - Fl0, C0, P.lam_s, P.lam_l, P.lam_g);
+        const double Tw = P.wall_T[2];
+        double slope;
+        if (P.ny >= 2) {
+            const size_t k1 = (size_t)P.pitch + i;
+            double T1, Fl1;
+            invert_enthalpy<double, double>(P, he_get<R>(Heg, k1), (double)Cg[k1], T1, Fl1);
+            slope = (-8.0 * Tw + 9.0 * T0 - T1) / 3.0;
+        } else {
+            slope = (T0 - Tw) / 0.5;
+        }
+        Q = -lam * slope;
+    }
+    cols[i] = h;
+    cols[P.nx + i] = umax;
+    cols[2 * (size_t)P.nx + i] = Q;
+}
+
+// Reduces the per-column diagnostics of one case with one block of kDiagThreads
+// threads in a fixed order: H_m and U_max are maxima, Q_wall the sum of Q dx over the
+// wall faces.  Pe = U_max D / alpha_l with D = 2 R_0 and alpha_l = lambda_l/(rho_l C_p,l)
+// (Eq. 50, read with the largest droplet speed); Fo = lambda_l t/(rho_l C_p,l R_0^2).
+constexpr int kDiagThreads = 256;
+
+__global__ void __launch_bounds__(kDiagThreads) k_diag_finalize(const DevCase* __restrict__ dc,
+                                                                 const double* __restrict__ cols,
+                                                                 double R0, double* __restrict__ out) {
+    __shared__ double sh[3][kDiagThreads];
+    const int nx = dc->P.nx;
+    double h = 0.0, u = 0.0, q = 0.0;
+    for (int i = threadIdx.x; i < nx; i += kDiagThreads) {
+        h = fmax(h, cols[i]);
+        u = fmax(u, cols[nx + i]);
+        q += cols[2 * (size_t)nx + i];
+    }
+    sh[0][threadIdx.x] = h;
+    sh[1][threadIdx.x] = u;
+    sh[2][threadIdx.x] = q;
+    __syncthreads();
+    for (int w = kDiagThreads / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) {
+            sh[0][threadIdx.x] = fmax(sh[0][threadIdx.x], sh[0][threadIdx.x + w]);
+            sh[1][threadIdx.x] = fmax(sh[1][threadIdx.x], sh[1][threadIdx.x + w]);
+            sh[2][threadIdx.x] += sh[2][threadIdx.x + w];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        const CaseParams& P = dc->P;
+        const double alpha_l = P.lam_l / (P.rho_l * P.cp_l);
+        out[0] = sh[0][0];
+        out[1] = sh[1][0];
+        out[2] = sh[1][0] * 2.0 * R0 / alpha_l;
+        out[3] = P.lam_l * dc->stats[ST_T] / (P.rho_l * P.cp_l * R0 * R0);
+        out[4] = sh[2][0];
+    }
+}
+
 template <class R>
 __global__ void k_store(const DevCase* __restrict__ dc, uint32_t mask, const double* __restrict__ in) {
     int i, j;
@@ -121,7 +221,7 @@ __global__ void k_store(const DevCase* __restrict__ dc, uint32_t mask, const dou
         const double v = in[slot * N + o];
         switch (f) {
         case 0: phi_set<R>(dc, k, v); break;
-        case 1: static_cast<double*>(dc->He[0])[k] = v; break;
+        case 1: he_set<R>(dc->He[0], k, v); break;
         case 4: static_cast<R*>(dc->p[0])[k] = R(v); break;
         case 7: static_cast<R*>(dc->C[0])[k] = R(v); break;
         case 10: static_cast<R*>(dc->mx[0])[k] = R(v); break;
@@ -154,7 +254,7 @@ __global__ void k_stats_init(const DevCase* __restrict__ dc) {
     for (int j = 0; j < P.ny; ++j)
         for (int i = threadIdx.x; i < P.nx; i += blockDim.x) {
             const size_t k = (size_t)j * P.pitch + i;
-            const double He = static_cast<const double*>(dc->He[0])[k];
+            const double He = he_get<R>(dc->He[0], k);
             const R C = static_cast<const R*>(dc->C[0])[k];
             R T, Fl;
             invert_enthalpy<R, double>(P, He, C, T, Fl);
@@ -182,26 +282,33 @@ __global__ void k_stats_init(const DevCase* __restrict__ dc) {
     }
 }
 
-// step end: fixed-order sum of the stage-tile partials, Eq. 51 liquid-fraction measure,
-// freezing time (first t with Q_L >= 0.99, linear between steps)
+// step end: fixed-order sum of the stage-tile partials (FP64, or FP32 pairs in mixed
+// precision, so that the long per-case loop issues no FP64 instruction), Eq. 51
+// liquid-fraction measure, freezing time (first t with Q_L >= 0.99, linear between
+// steps)
+template <class R>
 __global__ void k_step_finalize(const DevCase* __restrict__ cases, const int* __restrict__ ids) {
-    __shared__ double sh[32];
+    using Slot = typename DSum<R>::Slot;
+    __shared__ Slot sh[32];
     const DevCase* dc = cases + ids[blockIdx.x];
-    double acc[kRedN];
-    for (int q = 0; q < kRedN; ++q) acc[q] = 0.0;
+    const Slot* red = static_cast<const Slot*>(dc->red);
+    DSum<R> acc[kRedN];
+    for (int q = 0; q < kRedN; ++q) acc[q] = DSum<R>::zero();
     for (int t = threadIdx.x; t < dc->red_tiles; t += blockDim.x)
-        for (int q = 0; q < kRedN; ++q) acc[q] += dc->red[(size_t)t * kRedN + q];
-    for (int q = 0; q < kRedN; ++q) acc[q] = block_sum(acc[q], sh);
+        for (int q = 0; q < kRedN; ++q) acc[q].add(DSum<R>::of(red[(size_t)t * kRedN + q]));
+    for (int q = 0; q < kRedN; ++q) acc[q] = block_sum0<R>(acc[q], sh);
     if (threadIdx.x == 0) {
+        double a[kRedN];
+        for (int q = 0; q < kRedN; ++q) a[q] = acc[q].value();
         double* st = dc->stats;
         const double dt = dc->P.dt;
-        st[ST_SUM_C] = acc[0];
-        st[ST_SUM_HE] = acc[1];
-        st[ST_SUM_FL_DROP] = acc[2];
-        st[ST_N_DROP] = acc[3];
-        const double QL = acc[3] > 0.0 ? acc[4] / acc[3] : 0.0;
+        st[ST_SUM_C] = a[0];
+        st[ST_SUM_HE] = a[1];
+        st[ST_SUM_FL_DROP] = a[2];
+        st[ST_N_DROP] = a[3];
+        const double QL = a[3] > 0.0 ? a[4] / a[3] : 0.0;
         st[ST_Q_L] = QL;
-        if (acc[5] > 0.0) st[ST_NONFINITE] = 1.0;
+        if (a[5] > 0.0) st[ST_NONFINITE] = 1.0;
         st[ST_T] += dt;
         st[ST_STEP] += 1.0;
         if (st[ST_T_FREEZE] < 0.0 && QL >= 0.99) {
@@ -235,6 +342,15 @@ cudaError_t launch_derive_fields(int prec, const DevCase* d, int nx, int ny, uin
     return cudaGetLastError();
 }
 
+cudaError_t launch_diagnostics(int prec, const DevCase* d, int nx, double R0, double* cols, double* out5,
+                               cudaStream_t st) {
+    const int nb = (nx + 127) / 128;
+    if (prec == 0) k_diag_columns<double><<<nb, 128, 0, st>>>(d, cols);
+    else k_diag_columns<float><<<nb, 128, 0, st>>>(d, cols);
+    k_diag_finalize<<<1, kDiagThreads, 0, st>>>(d, cols, R0, out5);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_store_fields(int prec, const DevCase* d, int nx, int ny, uint32_t mask,
                                 const double* in, cudaStream_t st) {
     if (prec == 0) k_store<double><<<cell_grid(nx, ny), 128, 0, st>>>(d, mask, in);
@@ -250,9 +366,10 @@ cudaError_t launch_stats_init(int prec, const DevCase* d, int nx, int ny, cudaSt
     return cudaGetLastError();
 }
 
-cudaError_t launch_step_finalize(const DevCase* cases, const int* ids, int ncases, cudaStream_t st) {
+cudaError_t launch_step_finalize(int prec, const DevCase* cases, const int* ids, int ncases, cudaStream_t st) {
     if (ncases <= 0) return cudaSuccess;
-    k_step_finalize<<<ncases, 256, 0, st>>>(cases, ids);
+    if (prec == 0) k_step_finalize<double><<<ncases, 256, 0, st>>>(cases, ids);
+    else k_step_finalize<float><<<ncases, 256, 0, st>>>(cases, ids);
     return cudaGetLastError();
 }
 

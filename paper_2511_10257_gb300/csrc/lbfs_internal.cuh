@@ -40,6 +40,9 @@ struct PhysT {
     R cp_s, cp_l, cp_g, chi_s, chi_l, chi_g;
     R beta, kappa, Q_g, cp_ref, dts, inv_dts, inv_cpref_dts, tau_g, dt, vol_ratio, gravity, T_m, L;
     R wall_T[4];
+    // the thresholds H_es = C_p,s T_m and L of Eq. 8 as (hi, lo) pairs of R: the exact
+    // FP64 value is hi + lo to FP32-pair accuracy (lo = 0 in FP64)
+    R Hes_hi, Hes_lo, L_hi, L_lo;
 };
 
 struct MGLevel {
@@ -67,9 +70,9 @@ struct DevCase {
     PhysT<double> qd;
     int nlev;
     MGLevel lev[kMaxLevels];
-    double* red;      // stage-tile partial sums, kRedN per tile
+    void* red;        // stage-tile partial sums, kRedN 8-byte DSum slots per tile
     int red_tiles;    // number of stage tiles of this case
-    double* mg_red;   // potential residual partial sums, 2 per fine tile
+    void* mg_red;     // potential residual partial sums, 2 DSum slots per fine tile
     int mg_tiles;
     double* stats;    // kStatN FP64 slots
 };
@@ -195,6 +198,153 @@ __device__ __forceinline__ void pair_add(float& sh, float& sl, float ph, float p
 __device__ __forceinline__ void pair_from(double v, float& h, float& l) {
     h = (float)v;
     l = (float)(v - (double)h);
+}
+
+// (hi, lo) + x for an FP32 x, renormalised (|lo| <= ulp(hi)/2)
+__device__ __forceinline__ float2 pair_add_f(float2 a, float x) {
+    float s, e;
+    two_sum(a.x, x, s, e);
+    e = __fadd_rn(e, a.y);
+    float2 r;
+    r.x = __fadd_rn(s, e);
+    r.y = __fsub_rn(e, __fsub_rn(r.x, s));
+    return r;
+}
+// (hi, lo) + (hi, lo), renormalised
+__device__ __forceinline__ float2 pair_add2(float2 a, float2 b) {
+    float2 r = a;
+    pair_add(r.x, r.y, b.x, b.y);
+    return r;
+}
+
+// ---- FP64-accurate sums ------------------------------------------------------------
+// FP64 in the FP64 mode.  In mixed precision an FP32 pair accumulated with error-free
+// additions (about 48 bits), so that no per-cell or per-tile FP64 instruction is
+// issued.  Slot is the 8-byte type of a partial sum kept in a global or shared buffer;
+// counts below 2^24 are exact in either.
+template <class R>
+struct DSum;
+template <>
+struct DSum<double> {
+    using Slot = double;
+    double v;
+    static __device__ __forceinline__ DSum zero() { DSum s; s.v = 0.0; return s; }
+    static __device__ __forceinline__ DSum of(Slot x) { DSum s; s.v = x; return s; }
+    static __device__ __forceinline__ DSum count(int n) { DSum s; s.v = (double)n; return s; }
+    __device__ __forceinline__ void add(double x) { v += x; }
+    __device__ __forceinline__ void add(DSum o) { v += o.v; }
+    __device__ __forceinline__ void sub(DSum o) { v -= o.v; }
+    __device__ __forceinline__ void shfl_add(int o) { v += __shfl_down_sync(0xffffffffu, v, o); }
+    __device__ __forceinline__ Slot slot() const { return v; }
+    __device__ __forceinline__ double value() const { return v; }
+};
+template <>
+struct DSum<float> {
+    using Slot = float2;
+    float2 v;
+    static __device__ __forceinline__ DSum zero() { DSum s; s.v.x = 0.0f; s.v.y = 0.0f; return s; }
+    static __device__ __forceinline__ DSum of(Slot x) { DSum s; s.v = x; return s; }
+    static __device__ __forceinline__ DSum count(int n) { DSum s; s.v.x = (float)n; s.v.y = 0.0f; return s; }
+    __device__ __forceinline__ void add(float x) { v = pair_add_f(v, x); }
+    __device__ __forceinline__ void add(float2 x) { v = pair_add2(v, x); }
+    __device__ __forceinline__ void add(DSum o) { v = pair_add2(v, o.v); }
+    __device__ __forceinline__ void sub(DSum o) {
+        float2 m;
+        m.x = -o.v.x;
+        m.y = -o.v.y;
+        v = pair_add2(v, m);
+    }
+    __device__ __forceinline__ void shfl_add(int o) {
+        float2 w;
+        w.x = __shfl_down_sync(0xffffffffu, v.x, o);
+        w.y = __shfl_down_sync(0xffffffffu, v.y, o);
+        v = pair_add2(v, w);
+    }
+    __device__ __forceinline__ Slot slot() const { return v; }
+    __device__ __forceinline__ double value() const { return (double)v.x + (double)v.y; }
+};
+
+// Block sum in a fixed order (warp shuffles, then the warps in index order); the
+// result is valid on thread 0 only.  sh: 32 slots of shared memory.
+template <class R>
+__device__ __forceinline__ DSum<R> block_sum0(DSum<R> v, typename DSum<R>::Slot* sh) {
+    for (int o = 16; o > 0; o >>= 1) v.shfl_add(o);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v.slot();
+    __syncthreads();
+    DSum<R> tot = DSum<R>::zero();
+    if (threadIdx.x == 0)
+        for (int q = 0; q < (int)((blockDim.x + 31) >> 5); ++q) tot.add(DSum<R>::of(sh[q]));
+    return tot;
+}
+
+// ---- enthalpy storage ------------------------------------------------------------
+// H_e is FP64 in the FP64 mode.  In mixed precision it is an FP32 pair (hi, lo),
+// hi = fl32(H_e) and lo = fl32(H_e - hi): about 48 significant bits, read, inverted
+// and updated on the FP32 pipes only (GB300's FP64 rate is a small fraction of its
+// FP32 rate).  Both take 8 bytes per cell.
+template <class R>
+struct HeStore;
+template <>
+struct HeStore<double> {
+    using T = double;
+};
+template <>
+struct HeStore<float> {
+    using T = float2;
+};
+__device__ __forceinline__ double he_value(double h) { return h; }
+__device__ __forceinline__ double he_value(float2 h) { return (double)h.x + (double)h.y; }
+template <class R>
+__device__ __forceinline__ double he_get(const void* base, size_t k) {
+    return he_value(static_cast<const typename HeStore<R>::T*>(base)[k]);
+}
+template <class R>
+__device__ __forceinline__ void he_set(void* base, size_t k, double v) {
+    if constexpr (sizeof(R) == 8) {
+        static_cast<double*>(base)[k] = v;
+    } else {
+        float2 h;
+        pair_from(v, h.x, h.y);
+        static_cast<float2*>(base)[k] = h;
+    }
+}
+
+// Eq. 8 (as invert_h) on an FP32-pair enthalpy.  Each threshold difference is formed
+// from the parts, (hi - t_hi) + (lo - t_lo): the high parts of two nearby values
+// subtract exactly, so the difference is within an FP32 rounding of the FP64 one,
+// and no FP64 instruction is needed.
+__device__ __forceinline__ void invert_hp(const PhysT<float>& Q, float2 He, float C, float& T, float& Fl,
+                                          float* He_r = nullptr) {
+    const float cpL = Q.cp_g + C * (Q.cp_l - Q.cp_g);
+    float ds, dl;
+    if (Q.T_m == 0.0f) {   // H_es = 0 and H_el = L
+        ds = __fadd_rn(He.x, He.y);
+        dl = __fadd_rn(__fsub_rn(He.x, Q.L_hi), __fsub_rn(He.y, Q.L_lo));
+        if (He_r) *He_r = ds;
+    } else {
+        float2 Hel;
+        Hel.x = Q.L_hi;
+        Hel.y = Q.L_lo;
+        Hel = pair_add_f(Hel, cpL * Q.T_m);
+        ds = __fadd_rn(__fsub_rn(He.x, Q.Hes_hi), __fsub_rn(He.y, Q.Hes_lo));
+        dl = __fadd_rn(__fsub_rn(He.x, Hel.x), __fsub_rn(He.y, Hel.y));
+        if (He_r) *He_r = ds + Q.Hes_hi;
+    }
+    if (C < 0.5f) {
+        Fl = 1.0f;
+        T = Q.T_m + fdiv(dl, cpL);
+    } else if (ds < 0.0f) {
+        Fl = 0.0f;
+        T = Q.T_m + fdiv(ds, Q.cp_s);
+    } else if (dl <= 0.0f) {
+        Fl = fdiv(ds, ds - dl);
+        T = Q.T_m;
+    } else {
+        Fl = 1.0f;
+        T = Q.T_m + fdiv(dl, cpL);
+    }
 }
 
 // master potential of cell k in FP64, whichever precision stores it

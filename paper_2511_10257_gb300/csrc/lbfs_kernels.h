@@ -22,7 +22,7 @@ constexpr int kMgTX = 32, kMgTY = 8;
 cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* tiles, int n,
                                  cudaStream_t st);
 // tol: the convergence test; a residual above fail_tol marks the case's solve failed
-cudaError_t launch_mg_finalize(const DevCase* cases, const int* case_ids, int ncases, double tol,
+cudaError_t launch_mg_finalize(int prec, const DevCase* cases, const int* case_ids, int ncases, double tol,
                                double fail_tol, int first, int* not_done, cudaStream_t st);
 cudaError_t launch_mg_coarsest(int prec, const DevCase* cases, const int* case_ids, int ncases,
                                int max_cells, cudaStream_t st);
@@ -48,7 +48,11 @@ cudaError_t launch_derive_fields(int prec, const DevCase* dcase, int nx, int ny,
 cudaError_t launch_store_fields(int prec, const DevCase* dcase, int nx, int ny, uint32_t mask,
                                 const double* in, cudaStream_t st);
 cudaError_t launch_stats_init(int prec, const DevCase* dcase, int nx, int ny, cudaStream_t st);
-cudaError_t launch_step_finalize(const DevCase* cases, const int* case_ids, int ncases,
+// Sec. 5 diagnostics of one case: per-column scratch cols (3 nx doubles) and out5 =
+// {H_m, U_max, Pe, Fo, Q_wall}; two launches.
+cudaError_t launch_diagnostics(int prec, const DevCase* dcase, int nx, double R0, double* cols,
+                               double* out5, cudaStream_t st);
+cudaError_t launch_step_finalize(int prec, const DevCase* cases, const int* case_ids, int ncases,
                                  cudaStream_t st);
 
 }  // namespace lbfs

@@ -111,9 +111,10 @@ __device__ __forceinline__ double residual_cell<double>(const DevCase* dc, const
     return b - (diag * pc - off);
 }
 
-template <>
-__device__ __forceinline__ double residual_cell<float>(const DevCase* dc, const CaseParams& P,
-                                                       const MGLevel& lv, int i, int j, double& b_out) {
+// mixed precision: r rounded to FP32 (it feeds the FP32 correction solve); b and its
+// FP64 wall terms only at cells next to a Dirichlet wall (has_b)
+__device__ __forceinline__ float residual_cell_f(const DevCase* dc, const CaseParams& P, const MGLevel& lv,
+                                                 int i, int j, double& b_out, bool& has_b) {
     const float* mu = static_cast<const float*>(lv.mu);
     const float* hi = static_cast<const float*>(dc->phi);
     const float* lo = dc->phi_lo;
@@ -121,6 +122,7 @@ __device__ __forceinline__ double residual_cell<float>(const DevCase* dc, const 
     const float mc = mu[k], hc = hi[k], lc = lo[k];
     float ah = 0.f, al = 0.f;   // A phi as a pair
     double b = 0.0;
+    has_b = false;
     for (int w = 0; w < 4; ++w) {
         int ii, jj;
         float c, nh, nl;
@@ -136,6 +138,7 @@ __device__ __forceinline__ double residual_cell<float>(const DevCase* dc, const 
             c = 2.f * mc;
             pair_from(pw, nh, nl);
             b += (double)c * pw;
+            has_b = true;
         } else {
             continue;
         }
@@ -147,54 +150,67 @@ __device__ __forceinline__ double residual_cell<float>(const DevCase* dc, const 
         pair_add(ah, al, p, pe);
     }
     b_out = b;
-    return (double)(-__fadd_rn(ah, al));
+    return -__fadd_rn(ah, al);
 }
 
 template <class M>
 __global__ void __launch_bounds__(kNT) k_residual64(const DevCase* __restrict__ cases,
                                                     const TileRef* __restrict__ tiles) {
-    __shared__ double sh[32];
+    using Slot = typename DSum<M>::Slot;
+    __shared__ Slot sh[32];
     const TileRef tr = tiles[blockIdx.x];
     const DevCase* dc = cases + tr.case_id;
     const CaseParams& P = dc->P;
     const MGLevel lv = dc->lev[0];
     const int i = tr.x0 + threadIdx.x % kMgTX, j = tr.y0 + threadIdx.x / kMgTX;
-    double r2 = 0.0, b2 = 0.0;
+    DSum<M> r2 = DSum<M>::zero(), b2 = DSum<M>::zero();
     if (i < lv.nx && j < lv.ny) {
-        double b;
-        const double r = residual_cell<M>(dc, P, lv, i, j, b);
         const size_t k = (size_t)j * lv.pitch + i;
-        static_cast<M*>(lv.r)[k] = M(r);
-        if (sizeof(M) == 8) {
-            r2 = r * r;
+        double b;
+        if constexpr (sizeof(M) == 8) {
+            const double r = residual_cell<double>(dc, P, lv, i, j, b);
+            static_cast<double*>(lv.r)[k] = r;
+            r2.add(r * r);
+            b2.add(b * b);
         } else {
-            const float rf = (float)r;
-            r2 = (double)(rf * rf);
+            bool has_b;
+            const float r = residual_cell_f(dc, P, lv, i, j, b, has_b);
+            static_cast<float*>(lv.r)[k] = r;
+            r2.add(r * r);
+            if (has_b) {
+                float2 bb;
+                pair_from(b * b, bb.x, bb.y);
+                b2.add(bb);
+            }
         }
-        b2 = b * b;
     }
-    r2 = block_sum(r2, sh);
-    b2 = block_sum(b2, sh);
+    r2 = block_sum0<M>(r2, sh);
+    b2 = block_sum0<M>(b2, sh);
     if (threadIdx.x == 0) {
-        dc->mg_red[2 * (size_t)tr.slot] = r2;
-        dc->mg_red[2 * (size_t)tr.slot + 1] = b2;
+        Slot* red = static_cast<Slot*>(dc->mg_red);
+        red[2 * (size_t)tr.slot] = r2.slot();
+        red[2 * (size_t)tr.slot + 1] = b2.slot();
     }
 }
 
 // one block per case: relative residual, convergence flag, cycle count
+template <class M>
 __global__ void k_mg_finalize(const DevCase* __restrict__ cases, const int* __restrict__ ids,
                               double tol, double fail_tol, int first, int* not_done) {
-    __shared__ double sh[32];
+    using Slot = typename DSum<M>::Slot;
+    __shared__ Slot sh[32];
     const DevCase* dc = cases + ids[blockIdx.x];
-    double r2 = 0.0, b2 = 0.0;
+    const Slot* red = static_cast<const Slot*>(dc->mg_red);
+    DSum<M> r2 = DSum<M>::zero(), b2 = DSum<M>::zero();
     for (int t = threadIdx.x; t < dc->mg_tiles; t += blockDim.x) {
-        r2 += dc->mg_red[2 * (size_t)t];
-        b2 += dc->mg_red[2 * (size_t)t + 1];
+        r2.add(DSum<M>::of(red[2 * (size_t)t]));
+        b2.add(DSum<M>::of(red[2 * (size_t)t + 1]));
     }
-    r2 = block_sum(r2, sh);
-    b2 = block_sum(b2, sh);
+    r2 = block_sum0<M>(r2, sh);
+    b2 = block_sum0<M>(b2, sh);
     if (threadIdx.x == 0) {
-        const double rel = b2 > 0.0 ? sqrt(r2 / b2) : sqrt(r2);
+        const double rr = r2.value(), bb = b2.value();
+        const double rel = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
         double* st = dc->stats;
         st[ST_POT_RESID] = rel;
         const bool done = rel <= tol;
@@ -521,10 +537,11 @@ cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* 
     return cudaGetLastError();
 }
 
-cudaError_t launch_mg_finalize(const DevCase* cases, const int* ids, int ncases, double tol,
+cudaError_t launch_mg_finalize(int prec, const DevCase* cases, const int* ids, int ncases, double tol,
                                double fail_tol, int first, int* not_done, cudaStream_t st) {
     if (ncases <= 0) return cudaSuccess;
-    k_mg_finalize<<<ncases, 256, 0, st>>>(cases, ids, tol, fail_tol, first, not_done);
+    if (prec == 0) k_mg_finalize<double><<<ncases, 256, 0, st>>>(cases, ids, tol, fail_tol, first, not_done);
+    else k_mg_finalize<float><<<ncases, 256, 0, st>>>(cases, ids, tol, fail_tol, first, not_done);
     return cudaGetLastError();
 }
 

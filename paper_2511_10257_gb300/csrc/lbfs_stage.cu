@@ -172,9 +172,37 @@ __device__ __forceinline__ void wall_flux(const PhysT<R>& Q, int dirichlet, cons
     F[0] = dirichlet ? -fdiv(lam, rho) * dT : R(0);
 }
 
+// Eq. 8 on the stored enthalpy: FP64 differences in the FP64 mode, FP32-pair
+// differences in mixed precision (the thresholds' lo parts are zero in FP64).
+template <class R>
+__device__ __forceinline__ void invert_state(const PhysT<R>& Q, typename HeStore<R>::T He, R C, R& T, R& Fl,
+                                             R* He_r = nullptr) {
+    if constexpr (sizeof(R) == 8)
+        invert_h<double, double>(Q, Q.Hes_hi, Q.L_hi, He, C, T, Fl, He_r);
+    else
+        invert_hp(Q, He, C, T, Fl, He_r);
+}
+
+// H_e's Runge-Kutta update: stage 1 W + dt R(W); later stages W^n + b ((W + dt R) - W^n)
+// (a W^n + b X with a + b = 1 exactly).  FP64 in the FP64 mode.  In mixed precision the
+// stage increment is small next to H_e and is formed in FP32 from the pairs'
+// difference (their high parts subtract exactly when close), then added to the pair.
+__device__ __forceinline__ double he_rk(int stage, double Hek, double He0, double dt, double Rw, double b) {
+    if (stage == 0) return Hek + dt * Rw;
+    return He0 + b * ((Hek + dt * Rw) - He0);
+}
+__device__ __forceinline__ float2 he_rk(int stage, float2 Hek, float2 He0, float dt, float Rw, float b) {
+    if (stage == 0) return pair_add_f(Hek, __fmul_rn(dt, Rw));
+    const float d = __fadd_rn(__fsub_rn(Hek.x, He0.x), __fsub_rn(Hek.y, He0.y));
+    return pair_add_f(He0, __fmul_rn(b, __fmaf_rn(dt, Rw, d)));
+}
+__device__ __forceinline__ bool he_finite(double h) { return isfinite(h); }
+__device__ __forceinline__ bool he_finite(float2 h) { return isfinite(h.x) && isfinite(h.y); }
+
 template <class R, class HR, int TX, int TY, int NT, int MINB, bool HALF>
 __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restrict__ cases,
-                                                         const TileRef* __restrict__ tiles, int stage) {
+                                                         const TileRef* __restrict__ tiles, int ntiles,
+                                                         int stage) {
     using Gm = Geom<TX, TY>;
     constexpr int RW = Gm::RW, RH = Gm::RH, RN = Gm::RN, NFX = Gm::NFX, NF = Gm::NF;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -185,7 +213,11 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
     __shared__ PhysT<R> Q;
     __shared__ double red_s[32][kRedN];
 
-    const TileRef tr = tiles[blockIdx.x];
+    // one tile per block, or (persistent launch) a grid of resident blocks striding over
+    // the tile list; shared memory is reused tile after tile
+    for (int tile_i = blockIdx.x; tile_i < ntiles; tile_i += gridDim.x) {
+    __syncthreads();
+    const TileRef tr = tiles[tile_i];
     const DevCase* dc = cases + tr.case_id;
     {
         const int* src = reinterpret_cast<const int*>(&dc->P);
@@ -206,7 +238,6 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
     __syncthreads();
     const int nx = P.nx, ny = P.ny, pitch = P.pitch;
     const int x0 = tr.x0, y0 = tr.y0;
-    const HR Hes_h = HR(P.cp_s) * HR(P.T_m), L_h = HR(P.L);
 
     // ---- phase 1: load the stage state with halo, ghost rules at walls ----------
     for (int k = threadIdx.x; k < RN; k += NT) {
@@ -258,7 +289,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         const R C = gC[gi];
         R T, Fl;
         R Hes;   // H_e for the reconstruction (enters only the interface T_f)
-        invert_h<R, HR>(Q, Hes_h, L_h, He, C, T, Fl, &Hes);
+        invert_state<R>(Q, He, C, T, Fl, &Hes);
         const R Fs = R(1) - Fl;
         const R rho = mix(Fs, C, Q.rho_s, Q.rho_l, Q.rho_g);
         const R rinv = fdiv(R(3), rho);
@@ -358,9 +389,10 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
     // ---- phase 4: R(W), sources, Runge-Kutta combination ------------------------
     const R c3 = R(1.0 / 3.0);
     const double b_rk = stage == 0 ? 1.0 : (stage == 1 ? 0.25 : 2.0 / 3.0);
+    const R b = R(b_rk);
     const R dt = Q.dt;
-    // step-end sums of this thread's cells: FP64 for C, H_e and F_l, counts as integers
-    double aC = 0.0, aH = 0.0, aF = 0.0;
+    // step-end sums of this thread's cells: C, H_e and F_l (FP64-accurate), counts
+    DSum<R> aC = DSum<R>::zero(), aH = DSum<R>::zero(), aF = DSum<R>::zero();
     int nDrop = 0, nBad = 0;
     HR* oHe = static_cast<HR*>(dc->He[out]);
     R* oP = static_cast<R*>(dc->p[out]);
@@ -417,10 +449,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         // stage input at this cell
         const HR Hek = gHe[gi];
         const R pk = gP[gi], mxk = gMx[gi], myk = gMy[gi], Ck = gC[gi];
-        HR Hen;
+        const HR Hen = he_rk(stage, Hek, stage == 0 ? Hek : bHe[gi], dt, Rw[0], b);
         R pn, mxn, myn, Cn;
         if (stage == 0) {
-            Hen = Hek + HR(dt) * HR(Rw[0]);
             pn = pk + dt * Rw[1];
             mxn = mxk + dt * Rw[2];
             myn = myk + dt * Rw[3];
@@ -428,11 +459,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         } else {
             // a W^n + b X written as W^n + b (X - W^n): a + b = 1 holds exactly, so a
             // steady state stays steady in FP32 (1/3 and 2/3 both round up in FP32)
-            const HR bH = HR(b_rk);
-            const R b = R(b_rk);
-            const HR He0 = bHe[gi];
             const R p0 = bP[gi], mx0 = bMx[gi], my0 = bMy[gi], C0 = bC[gi];
-            Hen = He0 + bH * ((Hek + HR(dt) * HR(Rw[0])) - He0);
             pn = p0 + b * ((pk + dt * Rw[1]) - p0);
             mxn = mx0 + b * ((mxk + dt * Rw[2]) - mx0);
             myn = my0 + b * ((myk + dt * Rw[3]) - my0);
@@ -441,20 +468,19 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         if (stage == 2) {
             // step end: solid held at rest, (rho u) <- (1 - F_s)(rho u)
             R Tn, Fln;
-            invert_h<R, HR>(Q, Hes_h, L_h, Hen, Cn, Tn, Fln);
+            invert_state<R>(Q, Hen, Cn, Tn, Fln);
             mxn *= Fln;
             myn *= Fln;
             const R Fsn = R(1) - Fln;
             R* mu0 = static_cast<R*>(dc->lev[0].mu);
             mu0[(size_t)gy * dc->lev[0].pitch + gx] = R(1) + mix(Fsn, Cn, Q.chi_s, Q.chi_l, Q.chi_g);
-            aC += (double)Cn;
-            aH += (double)Hen;
+            aC.add(Cn);
+            aH.add(Hen);
             if (Cn >= R(0.5)) {
-                aF += (double)Fln;
+                aF.add(Fln);
                 nDrop += 1;
             }
-            const bool fin = isfinite((double)Hen) && isfinite(pn) && isfinite(mxn) && isfinite(myn) &&
-                             isfinite(Cn);
+            const bool fin = he_finite(Hen) && isfinite(pn) && isfinite(mxn) && isfinite(myn) && isfinite(Cn);
             if (!fin) nBad += 1;
         }
         oHe[gi] = Hen;
@@ -464,35 +490,40 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         oC[gi] = Cn;
     }
     if (stage == 2) {
-        // block reduction of the diagnostics (FP64 sums and integer counts, fixed
-        // order); the droplet's solid sum is its cell count minus its liquid sum
+        // block reduction of the diagnostics (FP64-accurate sums and integer counts,
+        // fixed order); the droplet's solid sum is its cell count minus its liquid sum
+        using Slot = typename DSum<R>::Slot;
+        Slot* rs = reinterpret_cast<Slot*>(&red_s[0][0]);   // 8-byte slots either way
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
         for (int o = 16; o > 0; o >>= 1) {
-            aC += __shfl_down_sync(0xffffffffu, aC, o);
-            aH += __shfl_down_sync(0xffffffffu, aH, o);
-            aF += __shfl_down_sync(0xffffffffu, aF, o);
+            aC.shfl_add(o);
+            aH.shfl_add(o);
+            aF.shfl_add(o);
             nDrop += __shfl_down_sync(0xffffffffu, nDrop, o);
             nBad += __shfl_down_sync(0xffffffffu, nBad, o);
         }
         if (lane == 0) {
-            red_s[wid][0] = aC;
-            red_s[wid][1] = aH;
-            red_s[wid][2] = aF;
-            red_s[wid][3] = (double)nDrop;
-            red_s[wid][5] = (double)nBad;
+            rs[wid * kRedN + 0] = aC.slot();
+            rs[wid * kRedN + 1] = aH.slot();
+            rs[wid * kRedN + 2] = aF.slot();
+            rs[wid * kRedN + 3] = DSum<R>::count(nDrop).slot();
+            rs[wid * kRedN + 5] = DSum<R>::count(nBad).slot();
         }
         __syncthreads();
         if (threadIdx.x < kRedN && threadIdx.x != 4) {
-            double v = 0.0;
-            for (int w = 0; w < NT / 32; ++w) v += red_s[w][threadIdx.x];
-            dc->red[(size_t)tr.slot * kRedN + threadIdx.x] = v;
+            Slot* red = static_cast<Slot*>(dc->red) + (size_t)tr.slot * kRedN;
+            DSum<R> v = DSum<R>::zero();
+            for (int w = 0; w < NT / 32; ++w) v.add(DSum<R>::of(rs[w * kRedN + threadIdx.x]));
+            red[threadIdx.x] = v.slot();
             if (threadIdx.x == 2) {
-                double n = 0.0;
-                for (int w = 0; w < NT / 32; ++w) n += red_s[w][3];
-                dc->red[(size_t)tr.slot * kRedN + 4] = n - v;
+                DSum<R> n = DSum<R>::zero();
+                for (int w = 0; w < NT / 32; ++w) n.add(DSum<R>::of(rs[w * kRedN + 3]));
+                n.sub(v);
+                red[4] = n.slot();
             }
         }
     }
+    }  // tile loop
 }
 
 // ---- launch helpers ------------------------------------------------------------
@@ -508,29 +539,34 @@ struct StageShape {
 
 template <class R, class HR, int TX, int TY, int MINB, bool HALF>
 static cudaError_t launch_t(const DevCase* cases, const TileRef* tiles, int ntiles, int stage,
-                            cudaStream_t st) {
+                            bool persistent, cudaStream_t st) {
     using S = StageShape<TX, TY>;
     auto kern = stage_kernel<R, HR, TX, TY, S::NT, MINB, HALF>;
-    static bool attr_set = false;
+    static int resident = 0;   // blocks that fit the device at once (for persistent launches)
     const size_t sm = S::template smem<R>();
-    if (!attr_set) {
+    if (!resident) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
-        attr_set = true;
+        int dev = 0, nsm = 0, per = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, S::NT, sm)) != cudaSuccess) return e;
+        resident = nsm * (per > 0 ? per : 1);
     }
-    kern<<<ntiles, S::NT, sm, st>>>(cases, tiles, stage);
+    const int grid = persistent ? (ntiles < resident ? ntiles : resident) : ntiles;
+    kern<<<grid, S::NT, sm, st>>>(cases, tiles, ntiles, stage);
     return cudaGetLastError();
 }
 
 // Tile shapes the autotuner chooses from (id -> TX x TY cells per block, and the
 // number of blocks per SM the register budget is cut for).  All have at least 256
 // cells, so a case never has more stage tiles than with 16 x 16.
-static constexpr int kShapes = 7;
-static constexpr int kShapeW[kShapes] = {32, 32, 64, 16, 64, 16, 32};
-static constexpr int kShapeH[kShapes] = {8, 16, 8, 16, 4, 16, 8};
+static constexpr int kShapes = 9;
+static constexpr int kShapeW[kShapes] = {32, 32, 64, 16, 64, 16, 32, 16, 32};
+static constexpr int kShapeH[kShapes] = {8, 16, 8, 16, 4, 16, 8, 16, 8};
 
 int stage_tile_shapes() { return kShapes; }
 int stage_tile_w(int prec, int tile) {
@@ -546,28 +582,31 @@ template <class R, int MINB_SMALL, int MINB_X>
 static cudaError_t launch_prec(int tile, int half, const DevCase* cases, const TileRef* tiles, int ntiles,
                                int stage, cudaStream_t st) {
     constexpr bool T = true, F = false;
+    const bool pers = tile >= 7;   // shapes 7 and 8: persistent launches of shapes 5 and 6
+    if (tile == 7) tile = 5;
+    if (tile == 8) tile = 6;
     switch (tile) {
     case 1:
-        return half ? launch_t<R, double, 32, 16, 1, T>(cases, tiles, ntiles, stage, st)
-                    : launch_t<R, double, 32, 16, 1, F>(cases, tiles, ntiles, stage, st);
+        return half ? launch_t<R, typename HeStore<R>::T, 32, 16, 1, T>(cases, tiles, ntiles, stage, pers, st)
+                    : launch_t<R, typename HeStore<R>::T, 32, 16, 1, F>(cases, tiles, ntiles, stage, pers, st);
     case 2:
-        return half ? launch_t<R, double, 64, 8, 1, T>(cases, tiles, ntiles, stage, st)
-                    : launch_t<R, double, 64, 8, 1, F>(cases, tiles, ntiles, stage, st);
+        return half ? launch_t<R, typename HeStore<R>::T, 64, 8, 1, T>(cases, tiles, ntiles, stage, pers, st)
+                    : launch_t<R, typename HeStore<R>::T, 64, 8, 1, F>(cases, tiles, ntiles, stage, pers, st);
     case 3:
-        return half ? launch_t<R, double, 16, 16, MINB_SMALL, T>(cases, tiles, ntiles, stage, st)
-                    : launch_t<R, double, 16, 16, MINB_SMALL, F>(cases, tiles, ntiles, stage, st);
+        return half ? launch_t<R, typename HeStore<R>::T, 16, 16, MINB_SMALL, T>(cases, tiles, ntiles, stage, pers, st)
+                    : launch_t<R, typename HeStore<R>::T, 16, 16, MINB_SMALL, F>(cases, tiles, ntiles, stage, pers, st);
     case 4:
-        return half ? launch_t<R, double, 64, 4, MINB_SMALL, T>(cases, tiles, ntiles, stage, st)
-                    : launch_t<R, double, 64, 4, MINB_SMALL, F>(cases, tiles, ntiles, stage, st);
+        return half ? launch_t<R, typename HeStore<R>::T, 64, 4, MINB_SMALL, T>(cases, tiles, ntiles, stage, pers, st)
+                    : launch_t<R, typename HeStore<R>::T, 64, 4, MINB_SMALL, F>(cases, tiles, ntiles, stage, pers, st);
     case 5:
-        return half ? launch_t<R, double, 16, 16, MINB_X, T>(cases, tiles, ntiles, stage, st)
-                    : launch_t<R, double, 16, 16, MINB_X, F>(cases, tiles, ntiles, stage, st);
+        return half ? launch_t<R, typename HeStore<R>::T, 16, 16, MINB_X, T>(cases, tiles, ntiles, stage, pers, st)
+                    : launch_t<R, typename HeStore<R>::T, 16, 16, MINB_X, F>(cases, tiles, ntiles, stage, pers, st);
     case 6:
-        return half ? launch_t<R, double, 32, 8, MINB_X, T>(cases, tiles, ntiles, stage, st)
-                    : launch_t<R, double, 32, 8, MINB_X, F>(cases, tiles, ntiles, stage, st);
+        return half ? launch_t<R, typename HeStore<R>::T, 32, 8, MINB_X, T>(cases, tiles, ntiles, stage, pers, st)
+                    : launch_t<R, typename HeStore<R>::T, 32, 8, MINB_X, F>(cases, tiles, ntiles, stage, pers, st);
     default:
-        return half ? launch_t<R, double, 32, 8, MINB_SMALL, T>(cases, tiles, ntiles, stage, st)
-                    : launch_t<R, double, 32, 8, MINB_SMALL, F>(cases, tiles, ntiles, stage, st);
+        return half ? launch_t<R, typename HeStore<R>::T, 32, 8, MINB_SMALL, T>(cases, tiles, ntiles, stage, pers, st)
+                    : launch_t<R, typename HeStore<R>::T, 32, 8, MINB_SMALL, F>(cases, tiles, ntiles, stage, pers, st);
     }
 }
 

@@ -66,11 +66,16 @@ class CaseStats(ct.Structure):
                 ("pot_cycles", ct.c_int32), ("nonfinite", ct.c_int32)]
 
 
+class CaseDiag(ct.Structure):
+    _fields_ = [("H_m", ct.c_double), ("U_max", ct.c_double), ("Pe", ct.c_double),
+                ("Fo", ct.c_double), ("Q_wall", ct.c_double)]
+
+
 EXPORTS = ("lbfs_create", "lbfs_set_case", "lbfs_set_fields", "lbfs_step", "lbfs_fields",
-           "lbfs_last_launch_count", "lbfs_timing", "lbfs_timing_read", "lbfs_autotune",
+           "lbfs_diagnostics", "lbfs_last_launch_count", "lbfs_timing", "lbfs_timing_read", "lbfs_autotune",
            "lbfs_destroy", "lbfs_last_error")
-TILE_SHAPES = [(32, 8), (32, 16), (64, 8), (16, 16), (64, 4), (16, 16), (32, 8)]
-TILE_NAMES = ["32x8", "32x16", "64x8", "16x16", "64x4", "16x16/3", "32x8/3"]
+TILE_SHAPES = [(32, 8), (32, 16), (64, 8), (16, 16), (64, 4), (16, 16), (32, 8), (16, 16), (32, 8)]
+TILE_NAMES = ["32x8", "32x16", "64x8", "16x16", "64x4", "16x16/3", "32x8/3", "16x16/3p", "32x8/3p"]
 TIMING_STAGE, TIMING_POTENTIAL, TIMING_FINALIZE = range(3)
 
 _lib = None
@@ -90,6 +95,7 @@ def load(path: str = LIB_PATH):
     L.lbfs_set_fields.argtypes = [vp, ct.c_int32, ct.c_uint32, ct.POINTER(ct.c_double)]
     L.lbfs_step.argtypes = [vp, ct.c_int32, ct.POINTER(CaseStats)]
     L.lbfs_fields.argtypes = [vp, ct.c_int32, ct.c_uint32, ct.POINTER(ct.c_double)]
+    L.lbfs_diagnostics.argtypes = [vp, ct.c_int32, ct.POINTER(CaseDiag), ct.POINTER(ct.c_double)]
     L.lbfs_last_launch_count.argtypes = [vp]
     L.lbfs_last_launch_count.restype = ct.c_int64
     L.lbfs_destroy.argtypes = [vp]
@@ -100,7 +106,7 @@ def load(path: str = LIB_PATH):
     L.lbfs_autotune.argtypes = [vp, ct.c_int32, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_double), ct.c_int32]
     L.lbfs_timing_read.argtypes = [vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int32]
     for name in ("lbfs_create", "lbfs_set_case", "lbfs_set_fields", "lbfs_step", "lbfs_fields",
-                 "lbfs_timing", "lbfs_timing_read", "lbfs_autotune"):
+                 "lbfs_diagnostics", "lbfs_timing", "lbfs_timing_read", "lbfs_autotune"):
         getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -201,6 +207,30 @@ class Solver:
         mask = sum(1 << int(f) for f in ids)
         self._check(self._L.lbfs_set_fields(self._h, int(case_id), mask, _dptr(buf)))
 
+    def set_fields_packed(self, case_id: int, ids, packed: np.ndarray):
+        """import fields from one C-contiguous FP64 array of shape (len(ids), ny, nx),
+        ids in increasing order, passed to the library without a copy (e.g. pinned
+        host memory)"""
+        ids = [int(i) for i in ids]
+        ny, nx = self.shapes[case_id]
+        if (ids != sorted(ids) or packed.dtype != np.float64 or not packed.flags.c_contiguous
+                or packed.shape != (len(ids), ny, nx)):
+            raise ValueError("packed must be C-contiguous float64 of shape (len(ids), ny, nx), ids sorted")
+        mask = sum(1 << f for f in ids)
+        self._check(self._L.lbfs_set_fields(self._h, int(case_id), mask, _dptr(packed)))
+
+    def fields_into(self, case_id: int, ids, out: np.ndarray):
+        """export fields into a caller-owned C-contiguous FP64 array of shape
+        (len(ids), ny, nx), ids in increasing order (no intermediate copy)"""
+        ids = [int(i) for i in ids]
+        ny, nx = self.shapes[case_id]
+        if (ids != sorted(ids) or out.dtype != np.float64 or not out.flags.c_contiguous
+                or out.shape != (len(ids), ny, nx)):
+            raise ValueError("out must be C-contiguous float64 of shape (len(ids), ny, nx), ids sorted")
+        mask = sum(1 << f for f in ids)
+        self._check(self._L.lbfs_fields(self._h, int(case_id), mask, _dptr(out)))
+        return out
+
     def step(self, nsteps: int = 1, raise_on_error: bool = True):
         out = (CaseStats * self.max_cases)()
         st = self._L.lbfs_step(self._h, int(nsteps), out)
@@ -216,6 +246,13 @@ class Solver:
         mask = sum(1 << f for f in ids)
         self._check(self._L.lbfs_fields(self._h, int(case_id), mask, _dptr(out)))
         return {f: out[k] for k, f in enumerate(ids)}
+
+    def diagnostics(self, case_id: int = 0):
+        """Sec. 5 diagnostics: (dict of H_m, U_max, Pe, Fo, Q_wall; wall heat flux Q per column)."""
+        d = CaseDiag()
+        q = np.zeros(self.shapes[case_id][1])
+        self._check(self._L.lbfs_diagnostics(self._h, int(case_id), ct.byref(d), _dptr(q)))
+        return {n: getattr(d, n) for n, _ in CaseDiag._fields_}, q
 
     def field(self, case_id: int, fid: int) -> np.ndarray:
         return self.fields(case_id, [fid])[fid]

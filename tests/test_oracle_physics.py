@@ -18,6 +18,7 @@ from scipy.special import erf, erfc
 from scipy.optimize import brentq
 
 import oracle
+from golden import load as golden
 from paper_2511_10257_gb300 import inputs as I
 
 CS2 = 1.0 / 3.0
@@ -114,24 +115,40 @@ def test_neumann_moving_front():
 
 
 def test_neumann_paper_parameters():
-    """Sec. 4.1's set: alpha = 0.4, L = 250, T_b = -1, T_0 = 1, T_m = 0 (k = 0.0435),
-    on a lattice with 20 cells per unit length, compared at the paper's t = 5, 10, 15:
-    front position within 0.15 cell, liquid profile within 5e-3, mean error below 1e-3."""
-    alpha, L, nx, s = 0.4, 250.0, 240, 20.0
+    """Sec. 4.1's set (tests/golden/neumann_sec41.txt): alpha = 0.4, L = 250, T_b = -1,
+    T_0 = 1, T_m = 0, on a lattice with 20 cells per unit length, compared at the
+    paper's t = 5, 10, 15: front position within 0.15 cell, liquid profile within 5e-3,
+    mean error below 1e-3."""
+    g = golden.keyed("neumann_sec41.txt")
+    assert g["rho_l"] == g["rho_s"] == 1.0 and g["cp_l"] == g["cp_s"] == 1.0
+    assert g["alpha_s"] == g["alpha_l"]
+    alpha, L, Tb, T0, Tm = g["alpha_s"], g["L"], g["T_b"], g["T_0"], g["T_m"]
+    nx, s = 240, 20.0
     c = _conduction_case(nx, alpha, L)
+    assert c["wall_T"][0] == Tb and c["T_init"] == T0 and c["T_m"] == Tm
     o = oracle.Oracle(c)
-    k = neumann_k(1.0 / L, 1.0 / L, alpha, alpha)
-    assert k == pytest.approx(0.0435, abs=2e-4)
+    k = neumann_k((Tm - Tb) / L, (T0 - Tm) / L, alpha, alpha)
+    assert k == pytest.approx(g["k"], abs=1e-5)
     x = np.arange(nx) + 0.5
-    for t_paper in (5.0, 10.0, 15.0):
+    for t_paper in g["times"]:
         t_lat = t_paper * s * s
         o.step(int(round((t_lat - o.stats()["t"]) / c["dt"])))
-        T_exact, X = neumann_T(x, t_lat, k, -1.0, 1.0, 0.0, alpha, alpha)
+        T_exact, X = neumann_T(x, t_lat, k, Tb, T0, Tm, alpha, alpha)
         T = o.get(I.T)[0]
         Xs = np.sum(1.0 - o.get(I.FL)[0])
         err = np.abs(T - T_exact)
         assert abs(Xs - X) < 0.15
         assert err[x > X + 1].max() < 5e-3 and err.mean() < 1e-3
+
+
+def test_default_ratios_follow_table3():
+    """The lattice defaults take the solid/liquid ratios of Table 3
+    (tests/golden/table3_ferrofluid.txt) for density, heat capacity and conductivity."""
+    t = {r[0]: (float(r[1]), float(r[2])) for r in golden.rows("table3_ferrofluid.txt")}
+    d = I.DEFAULTS
+    assert d["rho_s"] / d["rho_l"] == pytest.approx(t["rho"][1] / t["rho"][0], rel=1e-15)
+    assert d["cp_s"] / d["cp_l"] == pytest.approx(t["cp"][1] / t["cp"][0], rel=1e-15)
+    assert d["lam_s"] / d["lam_l"] == pytest.approx(t["lambda"][1] / t["lambda"][0], rel=1e-15)
 
 
 def _shear_wave(flags=0, steps=2000):

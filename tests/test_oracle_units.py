@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
+from golden import load as golden
 from paper_2511_10257_gb300 import inputs as I
 
 EX = [0, 1, 0, -1, 0, 1, -1, -1, 1]
@@ -71,20 +72,12 @@ def test_mixture_special_cases():
     assert oracle.mix(0.5, 0.5, 7.0, 2.0, 5.0) == pytest.approx(0.5 * 7 + 0.25 * 2 + 0.25 * 5)
 
 
-# Eq. 8 with T_s = T_l = T_m; values worked out by hand from the printed piecewise map.
-EQ8_TABLE = [
-    # (T_m, L, cp_s, cp_l, cp_g, C, He) -> (T, Fl)
-    ((0.0, 10.0, 0.5, 1.0, 1.0, 1.0, -0.5), (-1.0, 0.0)),      # solid branch: T = He/cp_s
-    ((0.0, 10.0, 0.5, 1.0, 1.0, 1.0, 0.0), (0.0, 0.0)),        # solidus tie: F_l = 0
-    ((0.0, 10.0, 0.5, 1.0, 1.0, 1.0, 2.5), (0.0, 0.25)),       # mushy
-    ((0.0, 10.0, 0.5, 1.0, 1.0, 1.0, 10.0), (0.0, 1.0)),       # liquidus tie: F_l = 1
-    ((0.0, 10.0, 0.5, 1.0, 1.0, 1.0, 12.0), (2.0, 1.0)),       # liquid: T = (He - L)/cp_l
-    ((1.0, 4.0, 0.5, 2.0, 1.0, 1.0, 0.25), (0.5, 0.0)),        # H_es = 0.5: below -> T = He/cp_s
-    ((1.0, 4.0, 0.5, 2.0, 1.0, 1.0, 3.25), (1.0, 0.5)),        # H_el = 2 + 4 = 6, midpoint of [0.5, 6]
-    ((1.0, 4.0, 0.5, 2.0, 1.0, 1.0, 8.0), (2.0, 1.0)),         # liquid: 1 + (8 - 6)/2
-    ((0.0, 10.0, 0.5, 2.0, 1.0, 0.75, 11.75), (1.0, 1.0)),     # cp of the liquid mixture 1.75
-    ((0.0, 10.0, 0.5, 2.0, 1.0, 0.25, 8.75), (-1.0, 1.0)),     # gas cell: never solid; cp 1.25
-]
+# Eq. 8 with T_s = T_l = T_m; values worked out by hand (tests/golden/eq8_inversion.txt)
+EQ8_TABLE = [(args, expect) for args, expect, _ in golden.eq8_table()]
+
+
+def test_eq8_fixture_is_complete():
+    assert len(EQ8_TABLE) == 10
 
 
 @pytest.mark.parametrize("args,expect", EQ8_TABLE)
