@@ -2,7 +2,7 @@
 
 Default workload: the 4096 x 2048 sessile ferrofluid drop (R = 768, field at 45
 degrees, Bo_m = 1.0, chi = 1, Ste = 0.1) in mixed precision (FP32 bulk, FP64
-enthalpy storage and inversion, FP64-refined FP32 multigrid potential).  One step
+enthalpy accuracy from FP32 pairs, FP64-refined FP32 multigrid potential).  One step
 is one full time step of every cell: the potential solve and three Runge-Kutta
 stages.  The metric is cell-updates per second.
 
@@ -209,6 +209,42 @@ def run_reference(args):
     return 0
 
 
+def potential_compare(device: int, tol: float = 1e-8, chunk: int = 20000, max_iters: int = 2000000) -> dict:
+    """The paper's own magnetic solver (explicit pseudo-time magnetic LBFS) against the
+    multigrid solve on the 128x64 drop in FP64: time for each to produce the potential
+    from the far-field start, the pseudo-time iteration stopped once it is within tol
+    (relative L-infinity) of the multigrid result."""
+    from paper_2511_10257_gb300 import inputs as I
+    from paper_2511_10257_gb300 import lbfs
+
+    case = I.config_small()
+    s = lbfs.Solver(precision=lbfs.FP64, max_cases=1, device=device)
+    s.set_case(0, case)
+    s.timing(True)
+    st = s.step(1)[0]
+    mg_ms = s.timing_read()[lbfs.TIMING_POTENTIAL][0]
+    ref = s.field(0, I.PHI)
+    s.close()
+    mu_max = 1.0 + max(case["chi_l"], case["chi_s"], case["chi_g"])
+    dtau = 0.9 / (4.0 * mu_max)   # forward-Euler limit 1/(4 max mu_m)
+    s = lbfs.Solver(precision=lbfs.FP64, max_cases=1, device=device)
+    s.set_case(0, case)
+    iters, err = 0, float("inf")
+    t0 = time.perf_counter()
+    while iters < max_iters:
+        s.potential_pseudo_time(0, chunk, dtau)
+        iters += chunk
+        err = float(abs(s.field(0, I.PHI) - ref).max() / abs(ref).max())
+        if err <= tol:
+            break
+    pt_ms = 1e3 * (time.perf_counter() - t0)
+    s.close()
+    return {"case": "128x64 sessile drop R=24, vertical field, Bo_m=0.5, chi=1 (FP64, far-field start)",
+            "multigrid": {"ms": mg_ms, "cycles": st["pot_cycles"], "rel_residual": st["pot_resid"]},
+            "pseudo_time_lbfs": {"ms": pt_ms, "iters": iters, "dtau": dtau, "rel_error_vs_multigrid": err,
+                                 "tol": tol, "converged": err <= tol}}
+
+
 def run_gpu(args):
     import numpy as np
     import torch
@@ -351,6 +387,7 @@ def run_gpu(args):
         cpu = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"the same physics on a {sample['nx']}x{sample['ny']} grid "
                          f"(R={sample['radius']:g}), {args.cpu_steps} steps, {dt:.1f} s"}
+    pcmp = None if args.no_potential_compare or world > 1 else potential_compare(local)
     state_bytes = ncell * (8 + 4 * (8 if prec == 0 else 4))
     grid = f"{case['nx']}x{case['ny']}" if len(cases) == 1 else f"{len(cases)} cases, {ncell} cells"
     line = {
@@ -375,6 +412,7 @@ def run_gpu(args):
         "gpu_launches": launches,
         "clocks": clk,
         "fp64": fp64,
+        "potential_solvers": pcmp,
     }
     print(json.dumps(line))
     solver.close()
@@ -397,6 +435,8 @@ def main(argv=None):
     ap.add_argument("--sample-factor", type=int, default=16)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-potential-compare", action="store_true",
+                    help="skip the multigrid versus pseudo-time magnetic LBFS comparison")
     ap.add_argument("--tile", type=int, default=-1, help="stage tile shape id; -1: autotune")
     ap.add_argument("--graph", type=int, default=0,
                     help="1: replay recorded CUDA graphs (disables the per-kernel timing)")

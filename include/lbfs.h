@@ -176,6 +176,18 @@ typedef struct lbfs_case_diag {
  * receives Q per column, or NULL.  LBFS_EINVAL for an undefined case or a NULL out. */
 lbfs_status lbfs_diagnostics(lbfs_ctx* ctx, int32_t case_id, lbfs_case_diag* out, double* q_wall);
 
+/* The paper's own magnetic solver (Sec. 3.2, Eqs. 12-18), offered beside the multigrid
+ * solve that lbfs_step uses: `iters` explicit pseudo-time steps of Eq. 17,
+ * phi <- phi - dtau div F, applied to case case_id's stored potential, with the
+ * per-direction LBFS face flux of the magnetic distribution (equilibrium Eq. 13,
+ * reconstruction Eq. 44 at x_f - e_a dts from the upwind cell, interface value Eq. 45,
+ * tau = 1/2 + mu_f/(c_s^2 dts), starred distribution Eq. 16) and the coefficient
+ * mu_m = 1 + chi(C, F_s) of the current state.  Its fixed point is the potential the
+ * multigrid solve returns.  FP64 arithmetic in both precisions; the stable range is
+ * about dtau < 1/(4 max mu_m).  iters >= 0, dtau > 0, else LBFS_EINVAL; waits for
+ * completion. */
+lbfs_status lbfs_potential_pseudo_time(lbfs_ctx* ctx, int32_t case_id, int32_t iters, double dtau);
+
 /* Number of device kernel launches the last lbfs_step issued (graph nodes count). */
 int64_t lbfs_last_launch_count(const lbfs_ctx* ctx);
 

@@ -670,6 +670,23 @@ lbfs_status lbfs_diagnostics(lbfs_ctx* ctx, int32_t id, lbfs_case_diag* out, dou
     return LBFS_OK;
 }
 
+lbfs_status lbfs_potential_pseudo_time(lbfs_ctx* ctx, int32_t id, int32_t iters, double dtau) {
+    lbfs_status r = check_case(ctx, id);
+    if (r != LBFS_OK) return r;
+    Slot& s = ctx->slots[id];
+    if (!s.defined) return fail(ctx, LBFS_EINVAL, "case not defined");
+    if (iters < 0 || !(dtau > 0.0)) return fail(ctx, LBFS_EINVAL, "iters must be >= 0 and dtau > 0");
+    CK(cudaSetDevice(ctx->cfg.device));
+    const int nx = s.hd.P.nx, ny = s.hd.P.ny;
+    r = ensure_scratch(ctx, (size_t)nx * ny * sizeof(double));
+    if (r != LBFS_OK) return r;
+    CK(launch_mu_from_state(ctx->prec, ctx->d_cases + id, nx, ny, ctx->stream));
+    CK(launch_pseudo_time(ctx->prec, ctx->d_cases + id, nx, ny, iters, dtau, ctx->d_scratch, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    ctx->pot_fresh = true;   // the next step re-converges the potential from this state
+    return LBFS_OK;
+}
+
 lbfs_status lbfs_step(lbfs_ctx* ctx, int32_t nsteps, lbfs_case_stats* out) {
     if (!ctx) return LBFS_EINVAL;
     if (nsteps < 0) return fail(ctx, LBFS_EINVAL, "nsteps must be >= 0");

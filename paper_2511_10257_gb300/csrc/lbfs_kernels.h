@@ -22,6 +22,10 @@ constexpr int kMgTX = 32, kMgTY = 8;
 cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* tiles, int n,
                                  cudaStream_t st);
 // tol: the convergence test; a residual above fail_tol marks the case's solve failed
+// `iters` explicit pseudo-time steps of the paper's magnetic LBFS (Eqs. 12-18) on one
+// case, FP64 arithmetic; tmp holds nx*ny doubles.  2 launches per step.
+cudaError_t launch_pseudo_time(int prec, const DevCase* dcase, int nx, int ny, int iters, double dtau,
+                               double* tmp, cudaStream_t st);
 cudaError_t launch_mg_finalize(int prec, const DevCase* cases, const int* case_ids, int ncases, double tol,
                                double fail_tol, int first, int* not_done, cudaStream_t st);
 cudaError_t launch_mg_coarsest(int prec, const DevCase* cases, const int* case_ids, int ncases,

@@ -527,7 +527,116 @@ __global__ void __launch_bounds__(kNT) k_correct(const DevCase* __restrict__ cas
     }
 }
 
+// ---- the paper's own magnetic solver (Sec. 3.2, Eqs. 12-18) ----------------------
+// Explicit pseudo-time relaxation of Eq. 17, phi <- phi - dtau div F, with the LBFS
+// face flux of the magnetic distribution.  Per face (cell A below/left, B above/right,
+// normal n): the equilibrium w_a phi (Eq. 13) at the points x_f - e_a dts, each
+// reconstructed from its upwind cell with central gradients (Eq. 44); interface value
+// Eq. 45; tau = 1/2 + mu_f/(c_s^2 dts) (Eq. 12 with the arithmetic-mean face mu); the
+// starred distribution of Eq. 16.  Summed over the D2Q9 directions, the flux
+//   F = sum_a e_a.n phi*_a = (tau - 1/2) sum_a e_a.n w_a phi(x_f - e_a dts)
+// (the interface part carries sum_a e_a.n w_a = 0), and the three points on each side
+// average their tangential slopes out, leaving
+//   F = mu_f/(2 dts) [phi_A - phi_B + (1/2 - dts)(g_A + g_B)],  g = normal central slope,
+// the compact -mu_f (phi_B - phi_A) at dts = 1/2.  Walls: a Dirichlet face carries the
+// compact flux to the wall value half a cell away, an insulating face none; the ghost
+// layer for the slopes is 2 phi_w - phi (Dirichlet) or phi (insulating).  FP64
+// arithmetic in both precisions; out receives the new potential.
+template <class M>
+__device__ __forceinline__ double phi_cell(const DevCase* dc, const CaseParams& P, int nx, int ny, int i, int j) {
+    // phi at (i, j), which may be one cell outside the grid (ghost rules above)
+    int w = -1;
+    if (i < 0 || i >= nx) {
+        if (P.periodic_x) i = i < 0 ? i + nx : i - nx;
+        else w = i < 0 ? 0 : 1;
+    }
+    if (j < 0 || j >= ny) {
+        if (P.periodic_y) j = j < 0 ? j + ny : j - ny;
+        else w = j < 0 ? 2 : 3;
+    }
+    if (w < 0) return phi_get<M>(dc, (size_t)j * P.pitch + i);
+    const int ii = i < 0 ? 0 : (i >= nx ? nx - 1 : i), jj = j < 0 ? 0 : (j >= ny ? ny - 1 : j);
+    const double pin = phi_get<M>(dc, (size_t)jj * P.pitch + ii);
+    if (!P.mag_dir[w]) return pin;
+    const double wx = w == 0 ? 0.0 : (w == 1 ? (double)nx : ii + 0.5);
+    const double wy = w == 2 ? 0.0 : (w == 3 ? (double)ny : jj + 0.5);
+    return 2.0 * (-P.H0 * (wx * P.cos_t + wy * P.sin_t)) - pin;
+}
+
+template <class M>
+__global__ void k_pseudo_step(const DevCase* __restrict__ dc, double dtau, double* __restrict__ out) {
+    const CaseParams& P = dc->P;
+    const int nx = P.nx, ny = P.ny;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= nx) return;
+    const M* mu = static_cast<const M*>(dc->lev[0].mu);
+    const int mp = dc->lev[0].pitch;
+    const double dts = P.dts, c1 = 0.5 - dts;
+    const double pc = phi_cell<M>(dc, P, nx, ny, i, j);
+    const double mc = (double)mu[(size_t)j * mp + i];
+    double div = 0.0;
+    // faces 0 left, 1 right, 2 bottom, 3 top; F is the flux along +x / +y
+    for (int f = 0; f < 4; ++f) {
+        const bool xf = f < 2, hi = (f & 1) != 0;
+        const int ni = i + (xf ? (hi ? 1 : -1) : 0), nj = j + (xf ? 0 : (hi ? 1 : -1));
+        const bool wall = xf ? (!P.periodic_x && (ni < 0 || ni >= nx)) : (!P.periodic_y && (nj < 0 || nj >= ny));
+        double F;
+        if (wall) {
+            if (!P.mag_dir[f]) continue;
+            const double wx = f == 0 ? 0.0 : (f == 1 ? (double)nx : i + 0.5);
+            const double wy = f == 2 ? 0.0 : (f == 3 ? (double)ny : j + 0.5);
+            const double pw = -P.H0 * (wx * P.cos_t + wy * P.sin_t);
+            // compact flux to the wall half a cell away, along +x / +y
+            F = hi ? 2.0 * mc * (pc - pw) : -2.0 * mc * (pc - pw);
+        } else {
+            const int wi = ni < 0 ? ni + nx : (ni >= nx ? ni - nx : ni);
+            const int wj = nj < 0 ? nj + ny : (nj >= ny ? nj - ny : nj);
+            const double mn = (double)mu[(size_t)wj * mp + wi];
+            const double muf = 0.5 * (mc + mn);
+            // A is the lower/left cell of the face, B the upper/right one
+            const int ai = hi ? i : ni, aj = hi ? j : nj, bi = hi ? ni : i, bj = hi ? nj : j;
+            const int dx = xf ? 1 : 0, dy = xf ? 0 : 1;
+            const double pA = hi ? pc : phi_cell<M>(dc, P, nx, ny, ai, aj);
+            const double pB = hi ? phi_cell<M>(dc, P, nx, ny, bi, bj) : pc;
+            double gsum = 0.0;
+            if (c1 != 0.0) {
+                const double gA = 0.5 * (phi_cell<M>(dc, P, nx, ny, ai + dx, aj + dy) -
+                                         phi_cell<M>(dc, P, nx, ny, ai - dx, aj - dy));
+                const double gB = 0.5 * (phi_cell<M>(dc, P, nx, ny, bi + dx, bj + dy) -
+                                         phi_cell<M>(dc, P, nx, ny, bi - dx, bj - dy));
+                gsum = gA + gB;
+            }
+            F = muf / (2.0 * dts) * ((pA - pB) + c1 * gsum);
+        }
+        div += hi ? F : -F;
+    }
+    out[(size_t)j * nx + i] = pc - dtau * div;
+}
+
+template <class M>
+__global__ void k_pseudo_store(const DevCase* __restrict__ dc, const double* __restrict__ in) {
+    const CaseParams& P = dc->P;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x, j = blockIdx.y;
+    if (i >= P.nx) return;
+    phi_set<M>(dc, (size_t)j * P.pitch + i, in[(size_t)j * P.nx + i]);
+}
+
 }  // namespace
+
+cudaError_t launch_pseudo_time(int prec, const DevCase* d, int nx, int ny, int iters, double dtau, double* tmp,
+                               cudaStream_t st) {
+    const dim3 grid((nx + 127) / 128, ny);
+    for (int it = 0; it < iters; ++it) {
+        if (prec == 0) {
+            k_pseudo_step<double><<<grid, 128, 0, st>>>(d, dtau, tmp);
+            k_pseudo_store<double><<<grid, 128, 0, st>>>(d, tmp);
+        } else {
+            k_pseudo_step<float><<<grid, 128, 0, st>>>(d, dtau, tmp);
+            k_pseudo_store<float><<<grid, 128, 0, st>>>(d, tmp);
+        }
+    }
+    return cudaGetLastError();
+}
 
 cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* tiles, int n,
                                  cudaStream_t st) {

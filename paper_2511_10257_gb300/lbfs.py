@@ -72,7 +72,7 @@ class CaseDiag(ct.Structure):
 
 
 EXPORTS = ("lbfs_create", "lbfs_set_case", "lbfs_set_fields", "lbfs_step", "lbfs_fields",
-           "lbfs_diagnostics", "lbfs_last_launch_count", "lbfs_timing", "lbfs_timing_read", "lbfs_autotune",
+           "lbfs_diagnostics", "lbfs_potential_pseudo_time", "lbfs_last_launch_count", "lbfs_timing", "lbfs_timing_read", "lbfs_autotune",
            "lbfs_destroy", "lbfs_last_error")
 TILE_SHAPES = [(32, 8), (32, 16), (64, 8), (16, 16), (64, 4), (16, 16), (32, 8), (16, 16), (32, 8)]
 TILE_NAMES = ["32x8", "32x16", "64x8", "16x16", "64x4", "16x16/3", "32x8/3", "16x16/3p", "32x8/3p"]
@@ -96,6 +96,7 @@ def load(path: str = LIB_PATH):
     L.lbfs_step.argtypes = [vp, ct.c_int32, ct.POINTER(CaseStats)]
     L.lbfs_fields.argtypes = [vp, ct.c_int32, ct.c_uint32, ct.POINTER(ct.c_double)]
     L.lbfs_diagnostics.argtypes = [vp, ct.c_int32, ct.POINTER(CaseDiag), ct.POINTER(ct.c_double)]
+    L.lbfs_potential_pseudo_time.argtypes = [vp, ct.c_int32, ct.c_int32, ct.c_double]
     L.lbfs_last_launch_count.argtypes = [vp]
     L.lbfs_last_launch_count.restype = ct.c_int64
     L.lbfs_destroy.argtypes = [vp]
@@ -106,7 +107,7 @@ def load(path: str = LIB_PATH):
     L.lbfs_autotune.argtypes = [vp, ct.c_int32, ct.POINTER(ct.c_int32), ct.POINTER(ct.c_double), ct.c_int32]
     L.lbfs_timing_read.argtypes = [vp, ct.POINTER(ct.c_double), ct.POINTER(ct.c_int64), ct.c_int32]
     for name in ("lbfs_create", "lbfs_set_case", "lbfs_set_fields", "lbfs_step", "lbfs_fields",
-                 "lbfs_diagnostics", "lbfs_timing", "lbfs_timing_read", "lbfs_autotune"):
+                 "lbfs_diagnostics", "lbfs_potential_pseudo_time", "lbfs_timing", "lbfs_timing_read", "lbfs_autotune"):
         getattr(L, name).restype = ct.c_int
     _lib = L
     return L
@@ -253,6 +254,10 @@ class Solver:
         q = np.zeros(self.shapes[case_id][1])
         self._check(self._L.lbfs_diagnostics(self._h, int(case_id), ct.byref(d), _dptr(q)))
         return {n: getattr(d, n) for n, _ in CaseDiag._fields_}, q
+
+    def potential_pseudo_time(self, case_id: int, iters: int, dtau: float):
+        """the paper's pseudo-time magnetic LBFS: `iters` explicit steps on the stored potential"""
+        self._check(self._L.lbfs_potential_pseudo_time(self._h, int(case_id), int(iters), float(dtau)))
 
     def field(self, case_id: int, fid: int) -> np.ndarray:
         return self.fields(case_id, [fid])[fid]
