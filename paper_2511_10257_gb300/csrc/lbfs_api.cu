@@ -561,6 +561,8 @@ lbfs_status lbfs_set_case(lbfs_ctx* ctx, int32_t id, const lbfs_case_desc* desc)
     }
     add((void**)&hd.red, (size_t)red_cap * kRedN * sizeof(double));
     add((void**)&hd.mg_red, (size_t)hd.mg_tiles * 2 * sizeof(double));
+    add((void**)&hd.chunk, (size_t)kFinChunks * (kRedN + 2) * sizeof(double));
+    add((void**)&hd.tickets, 2 * sizeof(unsigned));
     Slot& s = ctx->slots[id];
     free_slot(ctx, s);
     drop_graph(ctx);

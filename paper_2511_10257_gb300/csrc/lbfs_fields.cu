@@ -233,90 +233,116 @@ __global__ void k_store(const DevCase* __restrict__ dc, uint32_t mask, const dou
     }
 }
 
-template <class T>
-__device__ __forceinline__ T block_sum(T v, T* sh) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    __syncthreads();
-    if (lane == 0) sh[wid] = v;
-    __syncthreads();
-    T tot = 0;
-    for (int q = 0; q < (int)((blockDim.x + 31) >> 5); ++q) tot += sh[q];
-    return tot;
-}
-
-// statistics of the stored state (one block): used after initialisation or import
+// statistics of the stored state, after initialisation or import: kFinChunks blocks
+// each sum a fixed range of rows (FP64, or FP32 pairs in mixed precision); the last
+// block to finish (a ticket, no waiting) sums the chunks in order and writes sum C,
+// sum H_e, the droplet sums and Q_L (Eq. 51), which also seeds the freezing-time
+// interpolation
 template <class R>
 __global__ void k_stats_init(const DevCase* __restrict__ dc) {
-    __shared__ double sh[32];
+    using Slot = typename DSum<R>::Slot;
+    using HS = typename HeStore<R>::T;
+    __shared__ Slot sh[32];
+    __shared__ bool last;
     const CaseParams& P = dc->P;
-    double sC = 0, sH = 0, sFl = 0, nd = 0, sFs = 0;
-    for (int j = 0; j < P.ny; ++j)
+    const int c = blockIdx.x;
+    const int j0 = (int)((long long)P.ny * c / kFinChunks), j1 = (int)((long long)P.ny * (c + 1) / kFinChunks);
+    DSum<R> acc[5];
+    for (int q = 0; q < 5; ++q) acc[q] = DSum<R>::zero();
+    const HS* He = static_cast<const HS*>(dc->He[0]);
+    const R* Cg = static_cast<const R*>(dc->C[0]);
+    for (int j = j0; j < j1; ++j)
         for (int i = threadIdx.x; i < P.nx; i += blockDim.x) {
             const size_t k = (size_t)j * P.pitch + i;
-            const double He = he_get<R>(dc->He[0], k);
-            const R C = static_cast<const R*>(dc->C[0])[k];
+            const R C = Cg[k];
             R T, Fl;
-            invert_enthalpy<R, double>(P, He, C, T, Fl);
-            sC += (double)C;
-            sH += He;
+            invert_enthalpy<R, double>(P, he_value(He[k]), C, T, Fl);
+            acc[0].add(C);
+            acc[1].add(He[k]);
             if (C >= R(0.5)) {
-                sFl += (double)Fl;
-                nd += 1.0;
-                sFs += (double)(R(1) - Fl);
+                acc[2].add(Fl);
+                acc[3].add(R(1));
+                acc[4].add(R(1) - Fl);
             }
         }
-    sC = block_sum(sC, sh);
-    sH = block_sum(sH, sh);
-    sFl = block_sum(sFl, sh);
-    nd = block_sum(nd, sh);
-    sFs = block_sum(sFs, sh);
+    for (int q = 0; q < 5; ++q) acc[q] = block_sum0<R>(acc[q], sh);
+    Slot* ch = static_cast<Slot*>(dc->chunk);
     if (threadIdx.x == 0) {
-        double* st = dc->stats;
-        st[ST_SUM_C] = sC;
-        st[ST_SUM_HE] = sH;
-        st[ST_SUM_FL_DROP] = sFl;
-        st[ST_N_DROP] = nd;
-        st[ST_Q_L] = nd > 0 ? sFs / nd : 0.0;
-        st[ST_QL_PREV] = st[ST_Q_L];
+        for (int q = 0; q < 5; ++q) ch[c * kRedN + q] = acc[q].slot();
+        __threadfence();
+        last = atomicAdd(&dc->tickets[0], 1u) == (unsigned)(kFinChunks - 1);
     }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double a[5];
+    for (int q = 0; q < 5; ++q) {
+        DSum<R> v = DSum<R>::zero();
+        for (int k = 0; k < kFinChunks; ++k) v.add(DSum<R>::of(ld_cg(&ch[k * kRedN + q])));
+        a[q] = v.value();
+    }
+    dc->tickets[0] = 0u;
+    double* st = dc->stats;
+    st[ST_SUM_C] = a[0];
+    st[ST_SUM_HE] = a[1];
+    st[ST_SUM_FL_DROP] = a[2];
+    st[ST_N_DROP] = a[3];
+    st[ST_Q_L] = a[3] > 0 ? a[4] / a[3] : 0.0;
+    st[ST_QL_PREV] = st[ST_Q_L];
 }
 
 // step end: fixed-order sum of the stage-tile partials (FP64, or FP32 pairs in mixed
-// precision, so that the long per-case loop issues no FP64 instruction), Eq. 51
-// liquid-fraction measure, freezing time (first t with Q_L >= 0.99, linear between
-// steps)
+// precision), Eq. 51 liquid-fraction measure, freezing time (first t with Q_L >= 0.99,
+// linear between steps).  kFinChunks blocks per case each sum a fixed contiguous range
+// of tiles; the block that finishes last (a ticket, no waiting) sums the chunk sums
+// in chunk order and updates the statistics, so the result does not depend on which
+// block is last.
 template <class R>
 __global__ void k_step_finalize(const DevCase* __restrict__ cases, const int* __restrict__ ids) {
     using Slot = typename DSum<R>::Slot;
     __shared__ Slot sh[32];
-    const DevCase* dc = cases + ids[blockIdx.x];
+    __shared__ bool last;
+    const DevCase* dc = cases + ids[blockIdx.y];
+    const int T = dc->red_tiles, c = blockIdx.x;
+    const int t0 = (int)((long long)T * c / kFinChunks), t1 = (int)((long long)T * (c + 1) / kFinChunks);
     const Slot* red = static_cast<const Slot*>(dc->red);
     DSum<R> acc[kRedN];
     for (int q = 0; q < kRedN; ++q) acc[q] = DSum<R>::zero();
-    for (int t = threadIdx.x; t < dc->red_tiles; t += blockDim.x)
+    for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x)
         for (int q = 0; q < kRedN; ++q) acc[q].add(DSum<R>::of(red[(size_t)t * kRedN + q]));
     for (int q = 0; q < kRedN; ++q) acc[q] = block_sum0<R>(acc[q], sh);
+    Slot* ch = static_cast<Slot*>(dc->chunk);
     if (threadIdx.x == 0) {
-        double a[kRedN];
-        for (int q = 0; q < kRedN; ++q) a[q] = acc[q].value();
-        double* st = dc->stats;
-        const double dt = dc->P.dt;
-        st[ST_SUM_C] = a[0];
-        st[ST_SUM_HE] = a[1];
-        st[ST_SUM_FL_DROP] = a[2];
-        st[ST_N_DROP] = a[3];
-        const double QL = a[3] > 0.0 ? a[4] / a[3] : 0.0;
-        st[ST_Q_L] = QL;
-        if (a[5] > 0.0) st[ST_NONFINITE] = 1.0;
-        st[ST_T] += dt;
-        st[ST_STEP] += 1.0;
-        if (st[ST_T_FREEZE] < 0.0 && QL >= 0.99) {
-            const double q0 = st[ST_QL_PREV];
-            st[ST_T_FREEZE] = (st[ST_T] - dt) + dt * (0.99 - q0) / (QL - q0);
-        }
-        st[ST_QL_PREV] = QL;
+        for (int q = 0; q < kRedN; ++q) ch[c * kRedN + q] = acc[q].slot();
+        __threadfence();
+        last = atomicAdd(&dc->tickets[0], 1u) == (unsigned)(kFinChunks - 1);
     }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    double a[kRedN];
+    for (int q = 0; q < kRedN; ++q) {
+        DSum<R> v = DSum<R>::zero();
+        for (int k = 0; k < kFinChunks; ++k) v.add(DSum<R>::of(ld_cg(&ch[k * kRedN + q])));
+        a[q] = v.value();
+    }
+    dc->tickets[0] = 0u;
+    double* st = dc->stats;
+    const double dt = dc->P.dt;
+    st[ST_SUM_C] = a[0];
+    st[ST_SUM_HE] = a[1];
+    st[ST_SUM_FL_DROP] = a[2];
+    st[ST_N_DROP] = a[3];
+    const double QL = a[3] > 0.0 ? a[4] / a[3] : 0.0;
+    st[ST_Q_L] = QL;
+    if (a[5] > 0.0) st[ST_NONFINITE] = 1.0;
+    st[ST_T] += dt;
+    st[ST_STEP] += 1.0;
+    if (st[ST_T_FREEZE] < 0.0 && QL >= 0.99) {
+        const double q0 = st[ST_QL_PREV];
+        st[ST_T_FREEZE] = (st[ST_T] - dt) + dt * (0.99 - q0) / (QL - q0);
+    }
+    st[ST_QL_PREV] = QL;
 }
 
 }  // namespace
@@ -361,15 +387,16 @@ cudaError_t launch_store_fields(int prec, const DevCase* d, int nx, int ny, uint
 cudaError_t launch_stats_init(int prec, const DevCase* d, int nx, int ny, cudaStream_t st) {
     (void)nx;
     (void)ny;
-    if (prec == 0) k_stats_init<double><<<1, 1024, 0, st>>>(d);
-    else k_stats_init<float><<<1, 1024, 0, st>>>(d);
+    if (prec == 0) k_stats_init<double><<<kFinChunks, 512, 0, st>>>(d);
+    else k_stats_init<float><<<kFinChunks, 512, 0, st>>>(d);
     return cudaGetLastError();
 }
 
 cudaError_t launch_step_finalize(int prec, const DevCase* cases, const int* ids, int ncases, cudaStream_t st) {
     if (ncases <= 0) return cudaSuccess;
-    if (prec == 0) k_step_finalize<double><<<ncases, 256, 0, st>>>(cases, ids);
-    else k_step_finalize<float><<<ncases, 256, 0, st>>>(cases, ids);
+    const dim3 grid(kFinChunks, ncases);
+    if (prec == 0) k_step_finalize<double><<<grid, 256, 0, st>>>(cases, ids);
+    else k_step_finalize<float><<<grid, 256, 0, st>>>(cases, ids);
     return cudaGetLastError();
 }
 

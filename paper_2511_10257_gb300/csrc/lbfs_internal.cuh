@@ -9,6 +9,7 @@ namespace lbfs {
 
 constexpr int kMaxLevels = 16;
 constexpr int kRedN = 6;        // per-tile partial sums of the step-end reduction
+constexpr int kFinChunks = 32;  // blocks per case that reduce the tile partials
 constexpr int kStatN = 16;      // per-case device statistics slots
 
 // statistics slots (FP64, per case)
@@ -73,6 +74,8 @@ struct DevCase {
     void* red;        // stage-tile partial sums, kRedN 8-byte DSum slots per tile
     int red_tiles;    // number of stage tiles of this case
     void* mg_red;     // potential residual partial sums, 2 DSum slots per fine tile
+    void* chunk;      // kFinChunks x (kRedN + 2) DSum slots: per-chunk sums of the partials
+    unsigned* tickets;  // [0] step-end, [1] residual: chunks done (the last one finalises)
     int mg_tiles;
     double* stats;    // kStatN FP64 slots
 };
@@ -279,6 +282,10 @@ __device__ __forceinline__ DSum<R> block_sum0(DSum<R> v, typename DSum<R>::Slot*
     return tot;
 }
 
+// load that bypasses L1 (data written by other blocks of the same launch)
+__device__ __forceinline__ double ld_cg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float2 ld_cg(const float2* p) { return __ldcg(p); }
+
 // ---- enthalpy storage ------------------------------------------------------------
 // H_e is FP64 in the FP64 mode.  In mixed precision it is an FP32 pair (hi, lo),
 // hi = fl32(H_e) and lo = fl32(H_e - hi): about 48 significant bits, read, inverted
@@ -294,6 +301,12 @@ template <>
 struct HeStore<float> {
     using T = float2;
 };
+template <class S>
+__device__ __forceinline__ S he_zero();
+template <>
+__device__ __forceinline__ double he_zero<double>() { return 0.0; }
+template <>
+__device__ __forceinline__ float2 he_zero<float2>() { return make_float2(0.0f, 0.0f); }
 __device__ __forceinline__ double he_value(double h) { return h; }
 __device__ __forceinline__ double he_value(float2 h) { return (double)h.x + (double)h.y; }
 template <class R>

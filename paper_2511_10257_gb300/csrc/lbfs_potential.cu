@@ -193,34 +193,53 @@ __global__ void __launch_bounds__(kNT) k_residual64(const DevCase* __restrict__ 
     }
 }
 
-// one block per case: relative residual, convergence flag, cycle count
+// relative residual, convergence flag, cycle count: kFinChunks blocks per case sum
+// fixed contiguous ranges of the tile partials; the last block to finish (a ticket,
+// no waiting) sums the chunk sums in chunk order and decides
 template <class M>
 __global__ void k_mg_finalize(const DevCase* __restrict__ cases, const int* __restrict__ ids,
                               double tol, double fail_tol, int first, int* not_done) {
     using Slot = typename DSum<M>::Slot;
     __shared__ Slot sh[32];
-    const DevCase* dc = cases + ids[blockIdx.x];
+    __shared__ bool last;
+    const DevCase* dc = cases + ids[blockIdx.y];
+    const int T = dc->mg_tiles, c = blockIdx.x;
+    const int t0 = (int)((long long)T * c / kFinChunks), t1 = (int)((long long)T * (c + 1) / kFinChunks);
     const Slot* red = static_cast<const Slot*>(dc->mg_red);
     DSum<M> r2 = DSum<M>::zero(), b2 = DSum<M>::zero();
-    for (int t = threadIdx.x; t < dc->mg_tiles; t += blockDim.x) {
+    for (int t = t0 + (int)threadIdx.x; t < t1; t += blockDim.x) {
         r2.add(DSum<M>::of(red[2 * (size_t)t]));
         b2.add(DSum<M>::of(red[2 * (size_t)t + 1]));
     }
     r2 = block_sum0<M>(r2, sh);
     b2 = block_sum0<M>(b2, sh);
+    Slot* ch = static_cast<Slot*>(dc->chunk) + kFinChunks * kRedN;
     if (threadIdx.x == 0) {
-        const double rr = r2.value(), bb = b2.value();
-        const double rel = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
-        double* st = dc->stats;
-        st[ST_POT_RESID] = rel;
-        const bool done = rel <= tol;
-        st[ST_POT_DONE] = done ? 1.0 : 0.0;
-        if (rel > fail_tol) st[ST_POT_FAIL] = 1.0;
-        if (first) st[ST_POT_CYCLES] = 0.0;
-        if (!done) {
-            st[ST_POT_CYCLES] += 1.0;
-            atomicAdd(not_done, 1);
-        }
+        ch[2 * c] = r2.slot();
+        ch[2 * c + 1] = b2.slot();
+        __threadfence();
+        last = atomicAdd(&dc->tickets[1], 1u) == (unsigned)(kFinChunks - 1);
+    }
+    __syncthreads();
+    if (!last || threadIdx.x != 0) return;
+    __threadfence();
+    DSum<M> R2 = DSum<M>::zero(), B2 = DSum<M>::zero();
+    for (int k = 0; k < kFinChunks; ++k) {
+        R2.add(DSum<M>::of(ld_cg(&ch[2 * k])));
+        B2.add(DSum<M>::of(ld_cg(&ch[2 * k + 1])));
+    }
+    dc->tickets[1] = 0u;
+    const double rr = R2.value(), bb = B2.value();
+    const double rel = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
+    double* st = dc->stats;
+    st[ST_POT_RESID] = rel;
+    const bool done = rel <= tol;
+    st[ST_POT_DONE] = done ? 1.0 : 0.0;
+    if (rel > fail_tol) st[ST_POT_FAIL] = 1.0;
+    if (first) st[ST_POT_CYCLES] = 0.0;
+    if (!done) {
+        st[ST_POT_CYCLES] += 1.0;
+        atomicAdd(not_done, 1);
     }
 }
 
@@ -649,8 +668,9 @@ cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* 
 cudaError_t launch_mg_finalize(int prec, const DevCase* cases, const int* ids, int ncases, double tol,
                                double fail_tol, int first, int* not_done, cudaStream_t st) {
     if (ncases <= 0) return cudaSuccess;
-    if (prec == 0) k_mg_finalize<double><<<ncases, 256, 0, st>>>(cases, ids, tol, fail_tol, first, not_done);
-    else k_mg_finalize<float><<<ncases, 256, 0, st>>>(cases, ids, tol, fail_tol, first, not_done);
+    const dim3 grid(kFinChunks, ncases);
+    if (prec == 0) k_mg_finalize<double><<<grid, 256, 0, st>>>(cases, ids, tol, fail_tol, first, not_done);
+    else k_mg_finalize<float><<<grid, 256, 0, st>>>(cases, ids, tol, fail_tol, first, not_done);
     return cudaGetLastError();
 }
 

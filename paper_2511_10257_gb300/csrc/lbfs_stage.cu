@@ -31,6 +31,59 @@ struct Geom {
 // the interface equilibria, so only the surrounding-point equilibria are summed per
 // direction.  HALF: the streaming step is half a cell, so the points of the
 // upwind cells sit on its centre line and the normal slopes drop out there.
+// One side of a face: the three points with e_a.n = SG at c (e_a.t = 0), c - h (e_a.t = +1)
+// and c + h (e_a.t = -1); weights 1/9 and 1/36 for SG = +-1, 4/9 and 1/9 for SG = 0, whose
+// centre point is the rest direction a = 0.  Adds the side's equilibria (Eqs. 20, 28,
+// 29) to the face sums: Sp = sum f_eq, Sjn/Sjt = sum e_n/e_t f_eq, SC_ = sum g_eq,
+// SH = sum h_eq, Ah/Ag = sum e_n h_eq / g_eq, BGn/BGt = sum (e_n; e_n e_t) w Gamma_a.
+// Each point's terms are formed unweighted and the weights applied once per side.
+template <class R, int SG>
+__device__ __forceinline__ void side_sums(const R c[7], const R h[7], R r0, R r1, R k0, R k1, R cpref, R Qg,
+                                          R& Sp, R& Sjn, R& Sjt, R& SC_, R& SH, R& Ah, R& Ag, R& BGn, R& BGt) {
+    constexpr bool REST = SG == 0;
+    const R w0 = REST ? R(4.0 / 9.0) : R(1.0 / 9.0), w1 = REST ? R(1.0 / 9.0) : R(1.0 / 36.0);
+    R F[3], Gm[3], Hh[3], Ga[3];
+    R heq0 = 0, geq0 = 0;
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int et = e == 0 ? 0 : (e == 1 ? 1 : -1);
+        R q[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) q[k] = et == 0 ? c[k] : (et > 0 ? c[k] - h[k] : c[k] + h[k]);
+        const R p = q[0], un = q[1], ut = q[2], C = q[3], mu = q[4], T = q[5];
+        const R rho = r0 + r1 * C, cp = k0 + k1 * C;
+        const R eu = R(SG) * un + R(et) * ut;
+        const R uu = un * un + ut * ut;
+        const R G = eu * (R(3) + R(4.5) * eu) - R(1.5) * uu;   // Gamma_a(u)
+        F[e] = p + rho * G * R(1.0 / 3.0);
+        Gm[e] = G;
+        Hh[e] = T * (cpref + cp * G);
+        Ga[e] = mu * Qg + C * eu;
+        if (REST && e == 0) {
+            // a = 0: g_eq = C - (5/3) mu Q_g, h_eq = H_e - C_p,ref T + w0 T (C_p,ref + C_p Gamma)
+            geq0 = C - R(5.0 / 3.0) * mu * Qg;
+            heq0 = c[6] - cpref * T + w0 * Hh[0];
+        }
+    }
+    const R Fs = w0 * F[0] + w1 * (F[1] + F[2]);
+    Sp += Fs;
+    Sjt += w1 * (F[1] - F[2]);
+    if (REST) {
+        SC_ += geq0 + R(3) * w1 * (Ga[1] + Ga[2]);
+        SH += heq0 + w1 * (Hh[1] + Hh[2]);
+    } else {
+        const R gs = R(3) * (w0 * Ga[0] + w1 * (Ga[1] + Ga[2]));
+        const R hs = w0 * Hh[0] + w1 * (Hh[1] + Hh[2]);
+        SC_ += gs;
+        SH += hs;
+        Sjn += R(SG) * Fs;
+        Ag += R(SG) * gs;
+        Ah += R(SG) * hs;
+        BGn += w0 * Gm[0] + w1 * (Gm[1] + Gm[2]);
+        BGt += R(SG) * w1 * (Gm[1] - Gm[2]);
+    }
+}
+
 template <class R, bool HALF>
 __device__ __forceinline__ void face_flux(const PhysT<R>& Q, const R* __restrict__ s, int RN, int kA,
                                           int sn, int st, bool xface, R& Fh, R& Fp, R& Fmn, R& Fmt,
@@ -64,72 +117,39 @@ __device__ __forceinline__ void face_flux(const PhysT<R>& Q, const R* __restrict
     const R FsA = s[SFS * RN + kA], FsB = s[SFS * RN + kB], Fsm = R(0.5) * (FsA + FsB);
     const R cpref = Q.cp_ref, Qg = Q.Q_g;
     const R rs = Q.rho_s, rl = Q.rho_l, rg = Q.rho_g, cs = Q.cp_s, cl = Q.cp_l, cg = Q.cp_g;
-    R Sp = 0, Sjn = 0, Sjt = 0, SC_ = 0, SH = 0, Ah = 0, Ag = 0;
-    R Bpn = 0, Bpt = 0, BGn = 0, BGt = 0;
+    // Eq. 11 at fixed F_s is affine in C: rho = ra + rb C, C_p = ca + cb C on each side
+    const R rA0 = rg + FsA * (rs - rg), rA1 = (R(1) - FsA) * (rl - rg);
+    const R rB0 = rg + FsB * (rs - rg), rB1 = (R(1) - FsB) * (rl - rg);
+    const R rM0 = rg + Fsm * (rs - rg), rM1 = (R(1) - Fsm) * (rl - rg);
+    const R cA0 = cg + FsA * (cs - cg), cA1 = (R(1) - FsA) * (cl - cg);
+    const R cB0 = cg + FsB * (cs - cg), cB1 = (R(1) - FsB) * (cl - cg);
+    const R cM0 = cg + Fsm * (cs - cg), cM1 = (R(1) - Fsm) * (cl - cg);
+    // the centre point of each side's three points: the cell value, moved along the
+    // normal by (1/2 - dts) cells when the streaming step is not half a cell
+    R cAv[7], cBv[7];
 #pragma unroll
-    for (int a = 0; a < 9; ++a) {
-        const int en = d2q9_ex(a), et = d2q9_ey(a);
-        const R w = R(d2q9_w(a));
-        R q[7];
-        R Fs;
-        if (en > 0) {
-            const R on = R(0.5) - dts;
-#pragma unroll
-            for (int k = 0; k < 7; ++k) {
-                q[k] = et == 0 ? vA[k] : (et > 0 ? vA[k] - hA[k] : vA[k] + hA[k]);
-                if (!HALF) q[k] += on * nA[k];
-            }
-            Fs = FsA;
-        } else if (en < 0) {
-            const R on = R(-0.5) + dts;
-#pragma unroll
-            for (int k = 0; k < 7; ++k) {
-                q[k] = et == 0 ? vB[k] : (et > 0 ? vB[k] - hB[k] : vB[k] + hB[k]);
-                if (!HALF) q[k] += on * nB[k];
-            }
-            Fs = FsB;
-        } else {
-#pragma unroll
-            for (int k = 0; k < 7; ++k) q[k] = et == 0 ? m0[k] : (et > 0 ? m0[k] - hs[k] : m0[k] + hs[k]);
-            Fs = Fsm;
-        }
-        const R p = q[0], un = q[1], ut = q[2], C = q[3], mu = q[4], T = q[5], He = q[6];
-        const R rho = mix(Fs, C, rs, rl, rg);
-        const R cp = mix(Fs, C, cs, cl, cg);
-        const R eu = R(en) * un + R(et) * ut;
-        const R uu = un * un + ut * ut;
-        const R G = eu * (R(3) + R(4.5) * eu) - R(1.5) * uu;   // Gamma_a(u)
-        const R feq = w * (p + rho * G * R(1.0 / 3.0));
-        R geq, heq;
-        if (a == 0) {
-            geq = C - R(5.0 / 3.0) * mu * Qg;
-            heq = He - cpref * T + w * (cpref * T - R(1.5) * cp * T * uu);
-        } else {
-            geq = R(3) * w * (mu * Qg + C * eu);
-            heq = w * T * (cpref + cp * G);
-        }
-        Sp += feq;
-        if (en != 0) Sjn += R(en) * feq;
-        if (et != 0) Sjt += R(et) * feq;
-        SC_ += geq;
-        SH += heq;
-        if (en != 0) {
-            Ah += R(en) * heq;
-            Ag += R(en) * geq;
-            Bpn += w * p;                 // en * en = 1
-            BGn += w * G;
-            if (et != 0) {
-                Bpt += R(en * et) * w * p;
-                BGt += R(en * et) * w * G;
-            }
+    for (int k = 0; k < 7; ++k) {
+        cAv[k] = vA[k];
+        cBv[k] = vB[k];
+        if (!HALF) {
+            cAv[k] += (R(0.5) - dts) * nA[k];
+            cBv[k] += (R(-0.5) + dts) * nB[k];
         }
     }
+    R Sp = 0, Sjn = 0, Sjt = 0, SC_ = 0, SH = 0, Ah = 0, Ag = 0, BGn = 0, BGt = 0;
+    side_sums<R, 1>(cAv, hA, rA0, rA1, cA0, cA1, cpref, Qg, Sp, Sjn, Sjt, SC_, SH, Ah, Ag, BGn, BGt);
+    side_sums<R, -1>(cBv, hB, rB0, rB1, cB0, cB1, cpref, Qg, Sp, Sjn, Sjt, SC_, SH, Ah, Ag, BGn, BGt);
+    side_sums<R, 0>(m0, hs, rM0, rM1, cM0, cM1, cpref, Qg, Sp, Sjn, Sjt, SC_, SH, Ah, Ag, BGn, BGt);
+    // sum over e_a.n != 0 of w_a p and of (e_a.n)(e_a.t) w_a p: the three points of a side
+    // carry the weights 1/9, 1/36, 1/36 and sit at c, c - h, c + h along t
+    const R Bpn = R(1.0 / 6.0) * (cAv[0] + cBv[0]);
+    const R Bpt = R(1.0 / 18.0) * (hB[0] - hA[0]);
     // Eq. 45: interface values
     const R Cf = SC_, pf = Sp, Hef = SH;
-    const R rhof = mix(Fsm, Cf, rs, rl, rg);
+    const R rhof = rM0 + rM1 * Cf;
     const R inv_rc = fdiv(R(3), rhof);                 // 1 / (rho_f c_s^2)
     const R ufn = Sjn * inv_rc, uft = Sjt * inv_rc;
-    const R cpf = mix(Fsm, Cf, cs, cl, cg);
+    const R cpf = cM0 + cM1 * Cf;
     const R lamf = mix(Fsm, Cf, Q.lam_s, Q.lam_l, Q.lam_g);
     const R muf = mix(Fsm, Cf, Q.mu_s, Q.mu_l, Q.mu_g);
     R Tf, Flf;
@@ -172,6 +192,19 @@ __device__ __forceinline__ void wall_flux(const PhysT<R>& Q, int dirichlet, cons
     F[0] = dirichlet ? -fdiv(lam, rho) * dT : R(0);
 }
 
+// Asynchronous copy of one 4- or 8-byte element from global to shared memory
+// (cp.async, cached in L1), and the wait for all of this thread's copies.
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T* smem, const T* gmem) {
+    static_assert(sizeof(T) == 4 || sizeof(T) == 8, "4- or 8-byte elements");
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    if constexpr (sizeof(T) == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Eq. 8 on the stored enthalpy: FP64 differences in the FP64 mode, FP32-pair
 // differences in mixed precision (the thresholds' lo parts are zero in FP64).
 template <class R>
@@ -199,6 +232,12 @@ __device__ __forceinline__ float2 he_rk(int stage, float2 Hek, float2 He0, float
 __device__ __forceinline__ bool he_finite(double h) { return isfinite(h); }
 __device__ __forceinline__ bool he_finite(float2 h) { return isfinite(h.x) && isfinite(h.y); }
 
+// byte offset of the prefetch area in the stage kernel's dynamic shared memory
+template <class R>
+__host__ __device__ constexpr size_t stage_pf_offset(int RN, int NF) {
+    return ((size_t)(NSH * RN + 5 * NF) * sizeof(R) + RN + 15) / 16 * 16;
+}
+
 template <class R, class HR, int TX, int TY, int NT, int MINB, bool HALF>
 __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restrict__ cases,
                                                          const TileRef* __restrict__ tiles, int ntiles,
@@ -209,14 +248,20 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
     R* s = reinterpret_cast<R*>(smem_raw);
     R* flux = s + NSH * RN;                                             // [5][NF]
     signed char* kind = reinterpret_cast<signed char*>(flux + 5 * NF);  // [RN]
+    constexpr int TXY = TX * TY;
+    HR* pf_h = reinterpret_cast<HR*>(smem_raw + stage_pf_offset<R>(RN, NF));  // [2][TXY]
+    R* pf_r = reinterpret_cast<R*>(pf_h + 2 * TXY);                          // [9][TXY]
     __shared__ CaseParams P;
     __shared__ PhysT<R> Q;
-    __shared__ double red_s[32][kRedN];
+    // step-end values of the tile's cells (last stage): C, F_l of droplet cells, H_e
+    __shared__ R red_c[TX * TY], red_f[TX * TY];
+    __shared__ HR red_h[TX * TY];
+    __shared__ int red_n[NT / 32][2];
+    static_assert(NT >= TX * TY, "phase 4 gives each thread at most one cell");
 
-    // one tile per block, or (persistent launch) a grid of resident blocks striding over
-    // the tile list; shared memory is reused tile after tile
-    for (int tile_i = blockIdx.x; tile_i < ntiles; tile_i += gridDim.x) {
-    __syncthreads();
+    // one tile per block
+    const int tile_i = blockIdx.x;
+    if (tile_i >= ntiles) return;
     const TileRef tr = tiles[tile_i];
     const DevCase* dc = cases + tr.case_id;
     {
@@ -238,9 +283,53 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
     __syncthreads();
     const int nx = P.nx, ny = P.ny, pitch = P.pitch;
     const int x0 = tr.x0, y0 = tr.y0;
+    const HR* bHe = static_cast<const HR*>(dc->He[0]);
+    const R* bP = static_cast<const R*>(dc->p[0]);
+    const R* bMx = static_cast<const R*>(dc->mx[0]);
+    const R* bMy = static_cast<const R*>(dc->my[0]);
+    const R* bC = static_cast<const R*>(dc->C[0]);
+    R* Fsp = static_cast<R*>(dc->Fs_prev);
+    R* Sdp = static_cast<R*>(dc->Sdot);
+
+    // ---- prefetch of the phase-4 operands of this thread's cell: asynchronous copies
+    // into shared memory that land while phases 1-3 run.  pf_h: stage input H_e, W^n
+    // H_e; pf_r: stage input p, m_x, m_y, C; F_s of the previous step (stage 1) or the
+    // lagged dF_s/dt (stages 2, 3); W^n p, m_x, m_y, C.
+    if (threadIdx.x < TXY) {
+        const int pc = threadIdx.x;
+        const int gx = x0 + pc % TX, gy = y0 + pc / TX;
+        if (gx < nx && gy < ny) {
+            const size_t gi = (size_t)gy * pitch + gx;
+            cp_async_elem(&pf_h[pc], gHe + gi);
+            cp_async_elem(&pf_r[0 * TXY + pc], gP + gi);
+            cp_async_elem(&pf_r[1 * TXY + pc], gMx + gi);
+            cp_async_elem(&pf_r[2 * TXY + pc], gMy + gi);
+            cp_async_elem(&pf_r[3 * TXY + pc], gC + gi);
+            if (stage == 0) {
+                cp_async_elem(&pf_r[4 * TXY + pc], static_cast<const R*>(Fsp) + gi);
+            } else {
+                cp_async_elem(&pf_r[4 * TXY + pc], static_cast<const R*>(Sdp) + gi);
+                cp_async_elem(&pf_h[TXY + pc], bHe + gi);
+                cp_async_elem(&pf_r[5 * TXY + pc], bP + gi);
+                cp_async_elem(&pf_r[6 * TXY + pc], bMx + gi);
+                cp_async_elem(&pf_r[7 * TXY + pc], bMy + gi);
+                cp_async_elem(&pf_r[8 * TXY + pc], bC + gi);
+            }
+        }
+    }
 
     // ---- phase 1: load the stage state with halo, ghost rules at walls ----------
-    for (int k = threadIdx.x; k < RN; k += NT) {
+    // All of a thread's region loads are issued before any is used (one memory latency
+    // per tile instead of one per region cell of the thread).
+    constexpr int ROUNDS = (RN + NT - 1) / NT;
+    HR lHe[ROUNDS];
+    R lC[ROUNDS], lP[ROUNDS], lMx[ROUNDS], lMy[ROUNDS], lPhi[ROUNDS];
+    size_t lGi[ROUNDS];
+    int lWall[ROUNDS];
+#pragma unroll
+    for (int i = 0; i < ROUNDS; ++i) {
+        const int k = threadIdx.x + i * NT;
+        if (k >= RN) break;
         const int lx = k % RW, ly = k / RW;
         const int gx = x0 - Gm::H + lx, gy = y0 - Gm::H + ly;
         int sx, sy, xs, ys;  // source cell and status: 0 inside, 1 ghost low, 2 ghost high, 3 far
@@ -284,17 +373,31 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         } else {
             kd = 5;
         }
+        kind[k] = kd;
         const size_t gi = (size_t)sy * pitch + sx;
-        const HR He = gHe[gi];
-        const R C = gC[gi];
+        lGi[i] = gi;
+        lWall[i] = wall;
+        lHe[i] = gHe[gi];
+        lC[i] = gC[gi];
+        lP[i] = gP[gi];
+        lMx[i] = gMx[gi];
+        lMy[i] = gMy[gi];
+        lPhi[i] = gPhi[gi];
+    }
+#pragma unroll
+    for (int i = 0; i < ROUNDS; ++i) {
+        const int k = threadIdx.x + i * NT;
+        if (k >= RN) break;
+        const R C = lC[i];
         R T, Fl;
         R Hes;   // H_e for the reconstruction (enters only the interface T_f)
-        invert_state<R>(Q, He, C, T, Fl, &Hes);
+        invert_state<R>(Q, lHe[i], C, T, Fl, &Hes);
         const R Fs = R(1) - Fl;
         const R rho = mix(Fs, C, Q.rho_s, Q.rho_l, Q.rho_g);
         const R rinv = fdiv(R(3), rho);
-        R u = gMx[gi] * rinv, v = gMy[gi] * rinv;
-        R phi = gPhi[gi];
+        R u = lMx[i] * rinv, v = lMy[i] * rinv;
+        R phi = lPhi[i];
+        const int wall = lWall[i];
         if (wall >= 0) {
             u = -u;
             v = -v;
@@ -302,13 +405,14 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
             const R cp = mix(Fs, C, Q.cp_s, Q.cp_l, Q.cp_g);
             Hes = cp * T + Q.L * (R(1) - Fs);
             if (P.mag_dir[wall]) {
+                const int sx = (int)(lGi[i] % (size_t)pitch), sy = (int)(lGi[i] / (size_t)pitch);
                 double wx = wall == 0 ? 0.0 : (wall == 1 ? (double)nx : sx + 0.5);
                 double wy = wall == 2 ? 0.0 : (wall == 3 ? (double)ny : sy + 0.5);
                 double pw = -P.H0 * (wx * P.cos_t + wy * P.sin_t);
                 phi = R(2.0 * pw) - phi;
             }
         }
-        s[SP * RN + k] = gP[gi];
+        s[SP * RN + k] = lP[i];
         s[SU * RN + k] = u;
         s[SV * RN + k] = v;
         s[SC * RN + k] = C;
@@ -317,7 +421,6 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         s[SFS * RN + k] = Fs;
         s[SRHO * RN + k] = rho;
         s[SPHI * RN + k] = phi;
-        kind[k] = kd;
     }
     __syncthreads();
     // ---- phase 2: mu_c and |H|^2 at inner cells -------------------------------
@@ -392,24 +495,24 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
     const R b = R(b_rk);
     const R dt = Q.dt;
     // step-end sums of this thread's cells: C, H_e and F_l (FP64-accurate), counts
-    DSum<R> aC = DSum<R>::zero(), aH = DSum<R>::zero(), aF = DSum<R>::zero();
     int nDrop = 0, nBad = 0;
     HR* oHe = static_cast<HR*>(dc->He[out]);
     R* oP = static_cast<R*>(dc->p[out]);
     R* oMx = static_cast<R*>(dc->mx[out]);
     R* oMy = static_cast<R*>(dc->my[out]);
     R* oC = static_cast<R*>(dc->C[out]);
-    const HR* bHe = static_cast<const HR*>(dc->He[0]);
-    const R* bP = static_cast<const R*>(dc->p[0]);
-    const R* bMx = static_cast<const R*>(dc->mx[0]);
-    const R* bMy = static_cast<const R*>(dc->my[0]);
-    const R* bC = static_cast<const R*>(dc->C[0]);
-    R* Fsp = static_cast<R*>(dc->Fs_prev);
-    R* Sdp = static_cast<R*>(dc->Sdot);
+    cp_async_wait_all();   // this thread's prefetched operands (its own cell only)
     for (int c = threadIdx.x; c < TX * TY; c += NT) {
         const int tx = c % TX, ty = c / TX;
         const int gx = x0 + tx, gy = y0 + ty;
-        if (gx >= nx || gy >= ny) continue;
+        if (gx >= nx || gy >= ny) {
+            if (stage == 2) {
+                red_c[c] = R(0);
+                red_f[c] = R(0);
+                red_h[c] = he_zero<HR>();
+            }
+            continue;
+        }
         const int k = (ty + Gm::H) * RW + tx + Gm::H;
         const int fl = ty * (TX + 1) + tx, fb = NFX + ty * TX + tx;
         R Rw[5];
@@ -434,11 +537,11 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         // previous step's F_s, which is then replaced by F_s^n
         R Sd;
         if (stage == 0) {
-            Sd = (Fs - Fsp[gi]) / dt;
+            Sd = (Fs - pf_r[4 * TXY + c]) / dt;
             Fsp[gi] = Fs;
             Sdp[gi] = Sd;
         } else {
-            Sd = Sdp[gi];
+            Sd = pf_r[4 * TXY + c];
         }
         const R vr = Q.vol_ratio;
         Rw[0] += cp * T * divu;
@@ -447,9 +550,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         Rw[3] += c3 * (-C * dmy + R(0.5) * chi * dhy + rho * Q.gravity - rho * v * Sd);
         Rw[4] += C * vr * Sd;
         // stage input at this cell
-        const HR Hek = gHe[gi];
-        const R pk = gP[gi], mxk = gMx[gi], myk = gMy[gi], Ck = gC[gi];
-        const HR Hen = he_rk(stage, Hek, stage == 0 ? Hek : bHe[gi], dt, Rw[0], b);
+        const HR Hek = pf_h[c];
+        const R pk = pf_r[0 * TXY + c], mxk = pf_r[1 * TXY + c], myk = pf_r[2 * TXY + c], Ck = pf_r[3 * TXY + c];
+        const HR Hen = he_rk(stage, Hek, stage == 0 ? Hek : pf_h[TXY + c], dt, Rw[0], b);
         R pn, mxn, myn, Cn;
         if (stage == 0) {
             pn = pk + dt * Rw[1];
@@ -459,7 +562,8 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         } else {
             // a W^n + b X written as W^n + b (X - W^n): a + b = 1 holds exactly, so a
             // steady state stays steady in FP32 (1/3 and 2/3 both round up in FP32)
-            const R p0 = bP[gi], mx0 = bMx[gi], my0 = bMy[gi], C0 = bC[gi];
+            const R p0 = pf_r[5 * TXY + c], mx0 = pf_r[6 * TXY + c], my0 = pf_r[7 * TXY + c],
+                    C0 = pf_r[8 * TXY + c];
             pn = p0 + b * ((pk + dt * Rw[1]) - p0);
             mxn = mx0 + b * ((mxk + dt * Rw[2]) - mx0);
             myn = my0 + b * ((myk + dt * Rw[3]) - my0);
@@ -474,12 +578,10 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
             const R Fsn = R(1) - Fln;
             R* mu0 = static_cast<R*>(dc->lev[0].mu);
             mu0[(size_t)gy * dc->lev[0].pitch + gx] = R(1) + mix(Fsn, Cn, Q.chi_s, Q.chi_l, Q.chi_g);
-            aC.add(Cn);
-            aH.add(Hen);
-            if (Cn >= R(0.5)) {
-                aF.add(Fln);
-                nDrop += 1;
-            }
+            red_c[c] = Cn;
+            red_h[c] = Hen;
+            red_f[c] = Cn >= R(0.5) ? Fln : R(0);
+            nDrop += Cn >= R(0.5) ? 1 : 0;
             const bool fin = he_finite(Hen) && isfinite(pn) && isfinite(mxn) && isfinite(myn) && isfinite(Cn);
             if (!fin) nBad += 1;
         }
@@ -490,80 +592,87 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         oC[gi] = Cn;
     }
     if (stage == 2) {
-        // block reduction of the diagnostics (FP64-accurate sums and integer counts,
-        // fixed order); the droplet's solid sum is its cell count minus its liquid sum
+        // block reduction of the diagnostics in a fixed order: the cell counts by warp
+        // (integers), then one warp per sum over the tile's cells (FP64, or FP32 pairs):
+        // each lane adds every 32nd cell, then the lanes combine.  The droplet's solid
+        // sum is its cell count minus its liquid sum.
         using Slot = typename DSum<R>::Slot;
-        Slot* rs = reinterpret_cast<Slot*>(&red_s[0][0]);   // 8-byte slots either way
         const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        for (int o = 16; o > 0; o >>= 1) {
-            aC.shfl_add(o);
-            aH.shfl_add(o);
-            aF.shfl_add(o);
-            nDrop += __shfl_down_sync(0xffffffffu, nDrop, o);
-            nBad += __shfl_down_sync(0xffffffffu, nBad, o);
-        }
+        nDrop = __reduce_add_sync(0xffffffffu, nDrop);
+        nBad = __reduce_add_sync(0xffffffffu, nBad);
         if (lane == 0) {
-            rs[wid * kRedN + 0] = aC.slot();
-            rs[wid * kRedN + 1] = aH.slot();
-            rs[wid * kRedN + 2] = aF.slot();
-            rs[wid * kRedN + 3] = DSum<R>::count(nDrop).slot();
-            rs[wid * kRedN + 5] = DSum<R>::count(nBad).slot();
+            red_n[wid][0] = nDrop;
+            red_n[wid][1] = nBad;
         }
         __syncthreads();
-        if (threadIdx.x < kRedN && threadIdx.x != 4) {
-            Slot* red = static_cast<Slot*>(dc->red) + (size_t)tr.slot * kRedN;
+        Slot* red = static_cast<Slot*>(dc->red) + (size_t)tr.slot * kRedN;
+        if (wid == 0) {
             DSum<R> v = DSum<R>::zero();
-            for (int w = 0; w < NT / 32; ++w) v.add(DSum<R>::of(rs[w * kRedN + threadIdx.x]));
-            red[threadIdx.x] = v.slot();
-            if (threadIdx.x == 2) {
-                DSum<R> n = DSum<R>::zero();
-                for (int w = 0; w < NT / 32; ++w) n.add(DSum<R>::of(rs[w * kRedN + 3]));
-                n.sub(v);
-                red[4] = n.slot();
+            for (int c = lane; c < TX * TY; c += 32) v.add(red_c[c]);
+            for (int o = 16; o > 0; o >>= 1) v.shfl_add(o);
+            if (lane == 0) red[0] = v.slot();
+        } else if (wid == 1) {
+            DSum<R> v = DSum<R>::zero();
+            for (int c = lane; c < TX * TY; c += 32) v.add(red_h[c]);
+            for (int o = 16; o > 0; o >>= 1) v.shfl_add(o);
+            if (lane == 0) red[1] = v.slot();
+        } else if (wid == 2) {
+            DSum<R> v = DSum<R>::zero();
+            for (int c = lane; c < TX * TY; c += 32) v.add(red_f[c]);
+            for (int o = 16; o > 0; o >>= 1) v.shfl_add(o);
+            if (lane == 0) {
+                int n = 0, nb = 0;
+                for (int w = 0; w < NT / 32; ++w) {
+                    n += red_n[w][0];
+                    nb += red_n[w][1];
+                }
+                DSum<R> sol = DSum<R>::count(n);
+                sol.sub(v);
+                red[2] = v.slot();
+                red[3] = DSum<R>::count(n).slot();
+                red[4] = sol.slot();
+                red[5] = DSum<R>::count(nb).slot();
             }
         }
     }
-    }  // tile loop
 }
 
 // ---- launch helpers ------------------------------------------------------------
 template <int TX, int TY>
 struct StageShape {
     static constexpr int NT = ((2 * TX * TY + TX + TY) / 2 + 31) / 32 * 32;
+    // region fields, face fluxes and cell kinds, then (16-byte aligned) the prefetched
+    // phase-4 operands: 2 enthalpies and 9 working-precision values per tile cell
     template <class R>
     static constexpr size_t smem() {
         using Gm = Geom<TX, TY>;
-        return (size_t)(NSH * Gm::RN + 5 * Gm::NF) * sizeof(R) + Gm::RN + 16;
+        return stage_pf_offset<R>(Gm::RN, Gm::NF) +
+               (size_t)TX * TY * (2 * sizeof(typename HeStore<R>::T) + 9 * sizeof(R));
     }
 };
 
 template <class R, class HR, int TX, int TY, int MINB, bool HALF>
-static cudaError_t launch_t(const DevCase* cases, const TileRef* tiles, int ntiles, int stage,
-                            bool persistent, cudaStream_t st) {
+static cudaError_t launch_t(const DevCase* cases, const TileRef* tiles, int ntiles, int stage, cudaStream_t st) {
     using S = StageShape<TX, TY>;
     auto kern = stage_kernel<R, HR, TX, TY, S::NT, MINB, HALF>;
-    static int resident = 0;   // blocks that fit the device at once (for persistent launches)
+    static bool configured = false;
     const size_t sm = S::template smem<R>();
-    if (!resident) {
+    if (!configured) {
         cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         if (e != cudaSuccess) return e;
         e = cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout,
                                  cudaSharedmemCarveoutMaxShared);
         if (e != cudaSuccess) return e;
-        int dev = 0, nsm = 0, per = 0;
-        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-        if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, S::NT, sm)) != cudaSuccess) return e;
-        resident = nsm * (per > 0 ? per : 1);
+        configured = true;
     }
-    const int grid = persistent ? (ntiles < resident ? ntiles : resident) : ntiles;
-    kern<<<grid, S::NT, sm, st>>>(cases, tiles, ntiles, stage);
+    kern<<<ntiles, S::NT, sm, st>>>(cases, tiles, ntiles, stage);
     return cudaGetLastError();
 }
 
 // Tile shapes the autotuner chooses from (id -> TX x TY cells per block, and the
-// number of blocks per SM the register budget is cut for).  All have at least 256
-// cells, so a case never has more stage tiles than with 16 x 16.
+// number of blocks per SM the register budget is cut for in mixed precision: 1 for
+// ids 0-2, 2 for 3-4, 3 for 5-6, 4 for 7-8).  All have 256 or more cells, so a case
+// never has more stage tiles than with 16 x 16.
 static constexpr int kShapes = 9;
 static constexpr int kShapeW[kShapes] = {32, 32, 64, 16, 64, 16, 32, 16, 32};
 static constexpr int kShapeH[kShapes] = {8, 16, 8, 16, 4, 16, 8, 16, 8};
@@ -578,43 +687,37 @@ int stage_tile_h(int prec, int tile) {
     return kShapeH[(tile >= 0 && tile < kShapes) ? tile : 0];
 }
 
-template <class R, int MINB_SMALL, int MINB_X>
+template <class R, int TX, int TY, int MINB>
+static cudaError_t launch_h(int half, const DevCase* cases, const TileRef* tiles, int ntiles, int stage,
+                            cudaStream_t st) {
+    using HR = typename HeStore<R>::T;
+    return half ? launch_t<R, HR, TX, TY, MINB, true>(cases, tiles, ntiles, stage, st)
+                : launch_t<R, HR, TX, TY, MINB, false>(cases, tiles, ntiles, stage, st);
+}
+
+// MINB2/3/4: the blocks per SM of ids 3-4, 5-6 and 7-8 (all 1 in FP64, whose
+// registers do not allow more)
+template <class R, int MINB2, int MINB3, int MINB4>
 static cudaError_t launch_prec(int tile, int half, const DevCase* cases, const TileRef* tiles, int ntiles,
                                int stage, cudaStream_t st) {
-    constexpr bool T = true, F = false;
-    const bool pers = tile >= 7;   // shapes 7 and 8: persistent launches of shapes 5 and 6
-    if (tile == 7) tile = 5;
-    if (tile == 8) tile = 6;
     switch (tile) {
-    case 1:
-        return half ? launch_t<R, typename HeStore<R>::T, 32, 16, 1, T>(cases, tiles, ntiles, stage, pers, st)
-                    : launch_t<R, typename HeStore<R>::T, 32, 16, 1, F>(cases, tiles, ntiles, stage, pers, st);
-    case 2:
-        return half ? launch_t<R, typename HeStore<R>::T, 64, 8, 1, T>(cases, tiles, ntiles, stage, pers, st)
-                    : launch_t<R, typename HeStore<R>::T, 64, 8, 1, F>(cases, tiles, ntiles, stage, pers, st);
-    case 3:
-        return half ? launch_t<R, typename HeStore<R>::T, 16, 16, MINB_SMALL, T>(cases, tiles, ntiles, stage, pers, st)
-                    : launch_t<R, typename HeStore<R>::T, 16, 16, MINB_SMALL, F>(cases, tiles, ntiles, stage, pers, st);
-    case 4:
-        return half ? launch_t<R, typename HeStore<R>::T, 64, 4, MINB_SMALL, T>(cases, tiles, ntiles, stage, pers, st)
-                    : launch_t<R, typename HeStore<R>::T, 64, 4, MINB_SMALL, F>(cases, tiles, ntiles, stage, pers, st);
-    case 5:
-        return half ? launch_t<R, typename HeStore<R>::T, 16, 16, MINB_X, T>(cases, tiles, ntiles, stage, pers, st)
-                    : launch_t<R, typename HeStore<R>::T, 16, 16, MINB_X, F>(cases, tiles, ntiles, stage, pers, st);
-    case 6:
-        return half ? launch_t<R, typename HeStore<R>::T, 32, 8, MINB_X, T>(cases, tiles, ntiles, stage, pers, st)
-                    : launch_t<R, typename HeStore<R>::T, 32, 8, MINB_X, F>(cases, tiles, ntiles, stage, pers, st);
-    default:
-        return half ? launch_t<R, typename HeStore<R>::T, 32, 8, MINB_SMALL, T>(cases, tiles, ntiles, stage, pers, st)
-                    : launch_t<R, typename HeStore<R>::T, 32, 8, MINB_SMALL, F>(cases, tiles, ntiles, stage, pers, st);
+    case 1: return launch_h<R, 32, 16, 1>(half, cases, tiles, ntiles, stage, st);
+    case 2: return launch_h<R, 64, 8, 1>(half, cases, tiles, ntiles, stage, st);
+    case 3: return launch_h<R, 16, 16, MINB2>(half, cases, tiles, ntiles, stage, st);
+    case 4: return launch_h<R, 64, 4, MINB2>(half, cases, tiles, ntiles, stage, st);
+    case 5: return launch_h<R, 16, 16, MINB3>(half, cases, tiles, ntiles, stage, st);
+    case 6: return launch_h<R, 32, 8, MINB3>(half, cases, tiles, ntiles, stage, st);
+    case 7: return launch_h<R, 16, 16, MINB4>(half, cases, tiles, ntiles, stage, st);
+    case 8: return launch_h<R, 32, 8, MINB4>(half, cases, tiles, ntiles, stage, st);
+    default: return launch_h<R, 32, 8, 1>(half, cases, tiles, ntiles, stage, st);
     }
 }
 
 cudaError_t launch_stage(int prec, int tile, int half, const DevCase* cases, const TileRef* tiles,
                          int ntiles, int stage, cudaStream_t st) {
     if (ntiles <= 0) return cudaSuccess;
-    if (prec == 0) return launch_prec<double, 1, 1>(tile, half, cases, tiles, ntiles, stage, st);
-    return launch_prec<float, 2, 3>(tile, half, cases, tiles, ntiles, stage, st);
+    if (prec == 0) return launch_prec<double, 1, 1, 1>(tile, half, cases, tiles, ntiles, stage, st);
+    return launch_prec<float, 2, 3, 4>(tile, half, cases, tiles, ntiles, stage, st);
 }
 
 }  // namespace lbfs
