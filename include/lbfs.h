@@ -95,6 +95,11 @@ typedef struct lbfs_case_desc {
     double  mobility, Q_g;          /* M_c and the phase-field diffusion parameter          */
     double  gravity;                /* g along y (F_g = rho g)                              */
     double  dt, dts;                /* finite-volume step and streaming step                */
+    double  contact_angle_deg;      /* static contact angle theta_w at the walls, in (0, 180):
+                                       the phase-field ghost takes
+                                       C_in + (4/xi) cos(theta_w) C_in (1 - C_in) (the
+                                       equilibrium-profile wetting condition); 90 is the
+                                       no-flux (neutral) wall of Sec. 5                      */
     int32_t flags;                  /* must be 0                                            */
     int32_t pad_;
 } lbfs_case_desc;

@@ -51,7 +51,7 @@ class OracleCase(ct.Structure):
         ("chi_l", ct.c_double), ("chi_g", ct.c_double), ("chi_s", ct.c_double),
         ("sigma", ct.c_double), ("xi", ct.c_double), ("mobility", ct.c_double),
         ("Q_g", ct.c_double), ("gravity", ct.c_double),
-        ("dt", ct.c_double), ("dts", ct.c_double),
+        ("dt", ct.c_double), ("dts", ct.c_double), ("contact_angle_deg", ct.c_double),
         ("flags", ct.c_int32), ("pad_", ct.c_int32),
     ]
 

@@ -34,6 +34,7 @@ struct oracle_state {
     oracle_case cs;
     int nx, ny;
     double H0, L, beta, kappa, cos_t, sin_t, cp_ref, vol_ratio;
+    double wet;           /* 4 cos(theta_w)/xi of the wetting ghost rule (0 at 90 deg) */
     double* W[W_N];       /* evolved state, nx*ny */
     double* phi;          /* magnetic potential, nx*ny */
     double* Fs_prev;      /* F_s at the previous step */
@@ -160,7 +161,7 @@ static int needs_potential_solve(const oracle_state* s)
  * standard "-" is used (the literal sign is ORACLE_FLAG_LITERAL_MUC_SIGN). ---- */
 static void fill_ghosts(oracle_state* s, double* f, int kind);
 
-enum { GH_EVEN = 0, GH_ODD, GH_T, GH_HE };
+enum { GH_EVEN = 0, GH_ODD, GH_T, GH_HE, GH_WET };
 
 static void derive(oracle_state* s, double* const* W)
 {
@@ -184,7 +185,7 @@ static void derive(oracle_state* s, double* const* W)
             s->Fs[g] = Fs;
             s->rho[g] = rho;
         }
-    fill_ghosts(s, s->q[Q_C], GH_EVEN);
+    fill_ghosts(s, s->q[Q_C], GH_WET);
     double ksign = (c->flags & ORACLE_FLAG_LITERAL_MUC_SIGN) ? 1.0 : -1.0;
 #pragma omp parallel for num_threads(g_threads) if (g_threads > 1)
     for (int j = 0; j < ny; ++j)
@@ -217,9 +218,10 @@ static void derive(oracle_state* s, double* const* W)
 }
 
 /* ---- ghost layer.  Periodic axes wrap.  Walls: velocity no-slip (ghost = -inner),
- * p, C, mu_c, F_s, rho zero normal gradient (ghost = inner, theta = 90 deg), T
- * Dirichlet 2 T_w - T_in or adiabatic T_in, H_e rebuilt from the ghost T with the
- * inner C and F_s through H_e = C_p T + L (1 - F_s). ------------------------------ */
+ * p, mu_c, F_s, rho zero normal gradient (ghost = inner), C zero normal gradient at a
+ * contact angle of 90 deg and the wetting rule below otherwise, T Dirichlet
+ * 2 T_w - T_in or adiabatic T_in, H_e rebuilt from the ghost T with the inner C and
+ * F_s through H_e = C_p T + L (1 - F_s). -------------------------------------------- */
 static double ghost_value(oracle_state* s, const double* f, int kind, int wall, int ii, int jj)
 {
     const oracle_case* c = &s->cs;
@@ -235,6 +237,11 @@ static double ghost_value(oracle_state* s, const double* f, int kind, int wall, 
         double cp = oracle_mix(Fs, C, c->cp_s, c->cp_l, c->cp_g);
         return cp * Tg + s->L * (1.0 - Fs);
     }
+    case GH_WET:
+        /* wetting: the equilibrium profile C = (1 + tanh(2 d/xi))/2 meets the wall at the
+         * contact angle theta_w when dC/dn = -(4/xi) cos(theta_w) C (1 - C) there (n into
+         * the fluid); the ghost half a cell outside takes C_in - dC/dn, with C_in for C */
+        return f[g] + s->wet * f[g] * (1.0 - f[g]);
     default: return f[g];
     }
 }
@@ -806,6 +813,8 @@ int oracle_create(const oracle_case* cs, oracle_state** out)
     s->sin_t = sin(cs->field_angle_deg * ORACLE_PI / 180.0);
     s->cp_ref = 0.5 * (cs->cp_s + cs->cp_l);
     s->vol_ratio = 1.0 - cs->rho_s / cs->rho_l;
+    s->wet = cs->contact_angle_deg == 90.0 ? 0.0
+                                           : 4.0 * cos(cs->contact_angle_deg * ORACLE_PI / 180.0) / cs->xi;
     size_t N = (size_t)s->nx * s->ny;
     size_t NG = (size_t)(s->nx + 2) * (s->ny + 2);
     for (int n = 0; n < W_N; ++n) s->W[n] = (double*)calloc(N, sizeof(double));

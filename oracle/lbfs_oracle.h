@@ -48,6 +48,7 @@ typedef struct oracle_case {
     double  chi_l, chi_g, chi_s;
     double  sigma, xi, mobility, Q_g, gravity;
     double  dt, dts;                  /* finite-volume step and streaming step       */
+    double  contact_angle_deg;        /* static contact angle at the walls (90: none)  */
     int32_t flags;                    /* oracle-only reading switches (ORACLE_FLAG_*) */
     int32_t pad_;
 } oracle_case;

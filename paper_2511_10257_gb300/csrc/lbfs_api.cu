@@ -207,6 +207,11 @@ lbfs_status resolve(lbfs_ctx* ctx, const lbfs_case_desc& d, CaseParams& P) {
     P.sin_t = std::sin(ang);
     P.dt = d.dt;
     P.dts = d.dts;
+    if (!(d.contact_angle_deg > 0.0 && d.contact_angle_deg < 180.0))
+        return fail(ctx, LBFS_EINVAL, "contact_angle_deg must lie in (0, 180)");
+    // wetting: the equilibrium profile C = (1 + tanh(2 d/xi))/2 meets a wall at theta_w when
+    // dC/dn = -(4/xi) cos(theta_w) C (1 - C); 90 degrees is exactly the no-flux wall
+    P.wet = d.contact_angle_deg == 90.0 ? 0.0 : 4.0 * std::cos(d.contact_angle_deg * 3.14159265358979323846 / 180.0) / d.xi;
     P.cp_ref = 0.5 * (d.cp_s + d.cp_l);
     P.vol_ratio = 1.0 - d.rho_s / d.rho_l;
     bool chi = d.chi_l != 0.0 || d.chi_s != 0.0 || d.chi_g != 0.0;
@@ -241,6 +246,7 @@ void fill_phys(const CaseParams& P, PhysT<R>& q) {
     q.tau_g = R(0.5 + P.mobility / (P.Q_g * P.dts));
     q.dt = R(P.dt); q.vol_ratio = R(P.vol_ratio); q.gravity = R(P.gravity); q.T_m = R(P.T_m); q.L = R(P.L);
     for (int w = 0; w < 4; ++w) q.wall_T[w] = R(P.wall_T[w]);
+    q.wet = R(P.wet);
     const double Hes = P.cp_s * P.T_m;
     q.Hes_hi = R(Hes);
     q.Hes_lo = R(Hes - double(q.Hes_hi));

@@ -57,12 +57,14 @@ __global__ void k_mu_from_state(const DevCase* __restrict__ dc) {
 
 template <class R>
 __device__ __forceinline__ R C_at(const CaseParams& P, const R* C, int i, int j) {
-    // C with the zero-gradient (theta = 90 deg) ghost rule or periodic wrap
-    if (i < 0) i = P.periodic_x ? i + P.nx : 0;
-    if (i >= P.nx) i = P.periodic_x ? i - P.nx : P.nx - 1;
-    if (j < 0) j = P.periodic_y ? j + P.ny : 0;
-    if (j >= P.ny) j = P.periodic_y ? j - P.ny : P.ny - 1;
-    return C[(size_t)j * P.pitch + i];
+    // C with the wall ghost rule (wetting; zero gradient at 90 degrees) or periodic wrap
+    bool wall = false;
+    if (i < 0) { wall = !P.periodic_x; i = P.periodic_x ? i + P.nx : 0; }
+    if (i >= P.nx) { wall = !P.periodic_x; i = P.periodic_x ? i - P.nx : P.nx - 1; }
+    if (j < 0) { wall = wall || !P.periodic_y; j = P.periodic_y ? j + P.ny : 0; }
+    if (j >= P.ny) { wall = wall || !P.periodic_y; j = P.periodic_y ? j - P.ny : P.ny - 1; }
+    const R c = C[(size_t)j * P.pitch + i];
+    return wall ? c + R(P.wet) * c * (R(1) - c) : c;
 }
 
 template <class R>

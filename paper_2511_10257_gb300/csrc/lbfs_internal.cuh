@@ -31,6 +31,7 @@ struct CaseParams {
     double lam_l, lam_g, lam_s, chi_l, chi_g, chi_s;
     double beta, kappa, mobility, Q_g, gravity, T_m, L;
     double dt, dts, cp_ref, vol_ratio, H0, cos_t, sin_t;
+    double wet;                 // 4 cos(theta_w)/xi of the wetting ghost rule (0 at 90 deg)
 };
 
 // The per-point coefficients in the working precision R, converted once on the host
@@ -41,6 +42,7 @@ struct PhysT {
     R cp_s, cp_l, cp_g, chi_s, chi_l, chi_g;
     R beta, kappa, Q_g, cp_ref, dts, inv_dts, inv_cpref_dts, tau_g, dt, vol_ratio, gravity, T_m, L;
     R wall_T[4];
+    R wet;
     // the thresholds H_es = C_p,s T_m and L of Eq. 8 as (hi, lo) pairs of R: the exact
     // FP64 value is hi + lo to FP32-pair accuracy (lo = 0 in FP64)
     R Hes_hi, Hes_lo, L_hi, L_lo;

@@ -123,6 +123,23 @@ __device__ __forceinline__ float residual_cell_f(const DevCase* dc, const CasePa
     float ah = 0.f, al = 0.f;   // A phi as a pair
     double b = 0.0;
     has_b = false;
+    // (phi_c - phi_n) c added to A phi, error-free in pairs
+    auto term = [&](float c, float nh, float nl) {
+        float dh, de, p, pe;
+        two_sum(hc, -nh, dh, de);
+        const float dl = __fadd_rn(de, __fsub_rn(lc, nl));
+        two_prod(c, dh, p, pe);
+        pe = __fmaf_rn(c, dl, pe);
+        pair_add(ah, al, p, pe);
+    };
+    if (i > 0 && i < lv.nx - 1 && j > 0 && j < lv.ny - 1) {
+        // interior cell: four neighbour cells, no wall term (no FP64 instruction)
+        const size_t kw[4] = {k - 1, k + 1, k - lv.pitch, k + lv.pitch};
+#pragma unroll
+        for (int w = 0; w < 4; ++w) term(0.5f * (mc + mu[kw[w]]), hi[kw[w]], lo[kw[w]]);
+        b_out = 0.0;
+        return -__fadd_rn(ah, al);
+    }
     for (int w = 0; w < 4; ++w) {
         int ii, jj;
         float c, nh, nl;
@@ -142,12 +159,7 @@ __device__ __forceinline__ float residual_cell_f(const DevCase* dc, const CasePa
         } else {
             continue;
         }
-        float dh, de, p, pe;
-        two_sum(hc, -nh, dh, de);
-        const float dl = __fadd_rn(de, __fsub_rn(lc, nl));
-        two_prod(c, dh, p, pe);
-        pe = __fmaf_rn(c, dl, pe);
-        pair_add(ah, al, p, pe);
+        term(c, nh, nl);
     }
     b_out = b;
     return -__fadd_rn(ah, al);

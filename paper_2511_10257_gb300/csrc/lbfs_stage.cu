@@ -415,7 +415,8 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         s[SP * RN + k] = lP[i];
         s[SU * RN + k] = u;
         s[SV * RN + k] = v;
-        s[SC * RN + k] = C;
+        // a wall ghost's C follows the wetting rule (unchanged at 90 degrees, wet = 0)
+        s[SC * RN + k] = wall >= 0 ? C + Q.wet * C * (R(1) - C) : C;
         s[ST * RN + k] = T;
         s[SHE * RN + k] = Hes;
         s[SFS * RN + k] = Fs;
@@ -423,42 +424,44 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         s[SPHI * RN + k] = phi;
     }
     __syncthreads();
-    // ---- phase 2: mu_c and |H|^2 at inner cells -------------------------------
+    // ---- phase 2: mu_c and |H|^2 at inner cells; a wall ghost takes the values of
+    // the inner cell it mirrors (computed there again rather than copied, which saves
+    // a barrier) -------------------------------------------------------------------
     for (int k = threadIdx.x; k < RN; k += NT) {
-        const int lx = k % RW, ly = k / RW;
+        const int kd = kind[k];
+        int kk = k;
+        if (kd >= 1 && kd <= 4) {
+            const int w = kd - 1;
+            kk = k + (w == 0 ? 1 : w == 1 ? -1 : w == 2 ? RW : -RW);
+        }
+        const int lx = kk % RW, ly = kk / RW;
         R mu = 0, h2 = 0;
-        if (kind[k] == 0 && lx > 0 && lx < RW - 1 && ly > 0 && ly < RH - 1) {
+        if (kd <= 4 && kind[kk] == 0 && lx > 0 && lx < RW - 1 && ly > 0 && ly < RH - 1) {
             const R* c = s + SC * RN;
-            const R C = c[k];
-            const R lap = (c[k + 1] + c[k - 1]) + (c[k + RW] + c[k - RW]) - R(4) * C;
+            const R C = c[kk];
+            const R lap = (c[kk + 1] + c[kk - 1]) + (c[kk + RW] + c[kk - RW]) - R(4) * C;
             mu = R(2) * Q.beta * C * (C - R(1)) * (R(2) * C - R(1)) - Q.kappa * lap;
             const R* ph = s + SPHI * RN;
-            const R hx = R(-0.5) * (ph[k + 1] - ph[k - 1]);
-            const R hy = R(-0.5) * (ph[k + RW] - ph[k - RW]);
+            const R hx = R(-0.5) * (ph[kk + 1] - ph[kk - 1]);
+            const R hy = R(-0.5) * (ph[kk + RW] - ph[kk - RW]);
             h2 = hx * hx + hy * hy;
         }
         s[SMU * RN + k] = mu;
         s[SH2 * RN + k] = h2;
     }
     __syncthreads();
-    for (int k = threadIdx.x; k < RN; k += NT) {
-        const int kd = kind[k];
-        if (kd >= 1 && kd <= 4) {
-            const int w = kd - 1;
-            const int ks = k + (w == 0 ? 1 : w == 1 ? -1 : w == 2 ? RW : -RW);
-            const int sx = ks % RW, sy = ks / RW;
-            if (sx > 0 && sx < RW - 1 && sy > 0 && sy < RH - 1) {
-                s[SMU * RN + k] = s[SMU * RN + ks];
-                s[SH2 * RN + k] = s[SH2 * RN + ks];
-            }
-        }
-    }
-    __syncthreads();
     // ---- phase 3: face fluxes ------------------------------------------------------
+    // Face f is stored at flux index fs (x faces row by row, then y faces row by row).
+    // With 16-row tiles the threads take the faces column by column instead: a warp
+    // then reads two columns of 16 cells, whose shared-memory banks are all distinct
+    // because the region pitch RW is twice an odd number; the last y row follows.
+    constexpr bool COLS = TY == 16 && (RW % 4) == 2;
     for (int f = threadIdx.x; f < NF; f += NT) {
         R F[5] = {0, 0, 0, 0, 0};
+        int fs;
         if (f < NFX) {
-            const int fx = f % (TX + 1), ty = f / (TX + 1);
+            const int fx = COLS ? f / TY : f % (TX + 1), ty = COLS ? f % TY : f / (TX + 1);
+            fs = ty * (TX + 1) + fx;
             const int gxf = x0 + fx, gy = y0 + ty;
             if (gy < ny && gxf <= nx) {
                 const int kB = (ty + Gm::H) * RW + fx + Gm::H, kA = kB - 1;
@@ -472,7 +475,9 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
             }
         } else {
             const int g = f - NFX;
-            const int tx = g % TX, fy = g / TX;
+            const int tx = (COLS && g < TX * TY) ? g / TY : g % TX;
+            const int fy = (COLS && g < TX * TY) ? g % TY : g / TX;
+            fs = NFX + fy * TX + tx;
             const int gx = x0 + tx, gyf = y0 + fy;
             if (gx < nx && gyf <= ny) {
                 const int kB = (fy + Gm::H) * RW + tx + Gm::H, kA = kB - RW;
@@ -486,7 +491,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
             }
         }
 #pragma unroll
-        for (int c = 0; c < 5; ++c) flux[c * NF + f] = F[c];
+        for (int c = 0; c < 5; ++c) flux[c * NF + fs] = F[c];
     }
     __syncthreads();
     // ---- phase 4: R(W), sources, Runge-Kutta combination ------------------------

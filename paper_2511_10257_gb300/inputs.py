@@ -41,6 +41,7 @@ DEFAULTS = dict(
     chi_l=1.0, chi_g=0.0, chi_s=1.0,
     sigma=0.01, xi=4.0, mobility=0.05, Q_g=1.0, gravity=0.0,
     dt=0.5, dts=0.5,
+    contact_angle_deg=90.0,                  # neutral wetting (no-flux phase field)
 )
 
 
