@@ -280,8 +280,11 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
     const R* __restrict__ gMy = static_cast<const R*>(dc->my[in]);
     const R* __restrict__ gC = static_cast<const R*>(dc->C[in]);
     const R* __restrict__ gPhi = static_cast<const R*>(dc->phi);
-    __syncthreads();
-    const int nx = P.nx, ny = P.ny, pitch = P.pitch;
+    // the grid size and periodic flags in registers, read alongside the copy above, so
+    // that the prefetch and the halo loads below are issued before the copy lands (the
+    // barrier after the halo loads publishes P and Q)
+    const int nx = dc->P.nx, ny = dc->P.ny, pitch = dc->P.pitch;
+    const bool per_x = dc->P.periodic_x != 0, per_y = dc->P.periodic_y != 0;
     const int x0 = tr.x0, y0 = tr.y0;
     const HR* bHe = static_cast<const HR*>(dc->He[0]);
     const R* bP = static_cast<const R*>(dc->p[0]);
@@ -333,7 +336,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         const int lx = k % RW, ly = k / RW;
         const int gx = x0 - Gm::H + lx, gy = y0 - Gm::H + ly;
         int sx, sy, xs, ys;  // source cell and status: 0 inside, 1 ghost low, 2 ghost high, 3 far
-        if (P.periodic_x) {
+        if (per_x) {
             sx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
             xs = 0;
         } else if (gx >= 0 && gx < nx) {
@@ -345,7 +348,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         } else {
             sx = gx < 0 ? 0 : nx - 1; xs = 3;
         }
-        if (P.periodic_y) {
+        if (per_y) {
             sy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
             ys = 0;
         } else if (gy >= 0 && gy < ny) {
@@ -384,6 +387,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         lMy[i] = gMy[gi];
         lPhi[i] = gPhi[gi];
     }
+    __syncthreads();   // P and Q in shared memory
 #pragma unroll
     for (int i = 0; i < ROUNDS; ++i) {
         const int k = threadIdx.x + i * NT;
