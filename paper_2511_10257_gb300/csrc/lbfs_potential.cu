@@ -316,25 +316,28 @@ __device__ __forceinline__ int region_source(const CaseParams& P, int nx, int ny
     return 1;
 }
 
-// one red-black half-sweep of colour c over the region cells at least h from its edge
+// one red-black half-sweep of colour c over the region cells at least h from its edge.
+// Threads take only the cells of colour c (every other cell of a row), and a
+// neighbour is a cell exactly when its region entry lies inside the domain (in[]),
+// which is how the level's walls and periodic wraps were resolved at load time.
 template <class M, int H>
-__device__ __forceinline__ void region_half_sweep(const CaseParams& P, int nx, int ny, int x0, int y0,
-                                                  const M* mu, const M* r, M* e,
-                                                  const unsigned char* in, int c, int h) {
+__device__ __forceinline__ void region_half_sweep(const CaseParams& P, int x0, int y0, const M* mu, const M* r,
+                                                  M* e, const unsigned char* in, int c, int h) {
     using G = FRegion<H>;
-    for (int k = threadIdx.x; k < G::N; k += blockDim.x) {
-        const int lx = k % G::W, ly = k / G::W;
-        if (lx < h || lx >= G::W - h || ly < h || ly >= G::Hh - h || !in[k]) continue;
-        const int gx = x0 - H + lx, gy = y0 - H + ly;
-        if (((gx + gy) & 1) != c) continue;
+    const int VW = G::W - 2 * h, VH = G::Hh - 2 * h, HW = (VW + 1) / 2;
+    const int base = (x0 - H) + (y0 - H);
+    for (int t = threadIdx.x; t < HW * VH; t += blockDim.x) {
+        const int ly = h + t / HW;
+        const int lx = h + ((c - base - ly - h) & 1) + 2 * (t % HW);
+        if (lx >= G::W - h) continue;
+        const int k = ly * G::W + lx;
+        if (!in[k]) continue;
         const M mc = mu[k];
         M diag = 0, off = 0;
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
-            int ii, jj;
-            if (neighbour(P, nx, ny, gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx),
-                          gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy), w, ii, jj)) {
-                const int kn = k + (w == 0 ? -1 : w == 1 ? 1 : w == 2 ? -G::W : G::W);
+            const int kn = k + (w == 0 ? -1 : w == 1 ? 1 : w == 2 ? -G::W : G::W);
+            if (in[kn]) {
                 const M mf = M(0.5) * (mc + mu[kn]);
                 diag += mf;
                 off += mf * e[kn];
@@ -342,7 +345,7 @@ __device__ __forceinline__ void region_half_sweep(const CaseParams& P, int nx, i
                 diag += M(2) * mc;
             }
         }
-        e[k] = (r[k] + off) / diag;
+        e[k] = fdiv(r[k] + off, diag);
     }
 }
 
@@ -378,7 +381,7 @@ __global__ void __launch_bounds__(256) k_vdown(const DevCase* __restrict__ cases
     region_load<M, kHD>(P, lv, tr.x0, tr.y0, smu, sr, se, in, false);
     __syncthreads();
     for (int h = 1; h <= 2 * kFNu; ++h) {
-        region_half_sweep<M, kHD>(P, lv.nx, lv.ny, tr.x0, tr.y0, smu, sr, se, in, (h - 1) & 1, h);
+        region_half_sweep<M, kHD>(P, tr.x0, tr.y0, smu, sr, se, in, (h - 1) & 1, h);
         __syncthreads();
     }
     // pre-smoothed correction of the tile
@@ -406,14 +409,12 @@ __global__ void __launch_bounds__(256) k_vdown(const DevCase* __restrict__ cases
         for (int q = 0; q < 4; ++q) {
             const int lx = kHD + 2 * ci + (q & 1), ly = kHD + 2 * cj + (q >> 1);
             const int k = ly * G::W + lx;
-            const int i = 2 * I + (q & 1), j = 2 * J + (q >> 1);
             const M mc = smu[k], xc = se[k];
             M ax = 0;
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
-                int ii, jj;
-                if (neighbour(P, lv.nx, lv.ny, i, j, w, ii, jj)) {
-                    const int kn = k + (w == 0 ? -1 : w == 1 ? 1 : w == 2 ? -G::W : G::W);
+                const int kn = k + (w == 0 ? -1 : w == 1 ? 1 : w == 2 ? -G::W : G::W);
+                if (in[kn]) {
                     ax += M(0.5) * (mc + smu[kn]) * (xc - se[kn]);
                 } else if (P.mag_dir[w]) {
                     ax += M(2) * mc * xc;
@@ -467,7 +468,7 @@ __global__ void __launch_bounds__(256) k_vup(const DevCase* __restrict__ cases,
     }
     __syncthreads();
     for (int h = 1; h <= 2 * kFNu; ++h) {
-        region_half_sweep<M, kHU>(P, lv.nx, lv.ny, tr.x0, tr.y0, smu, sr, se, in, (h - 1) & 1, h);
+        region_half_sweep<M, kHU>(P, tr.x0, tr.y0, smu, sr, se, in, (h - 1) & 1, h);
         __syncthreads();
     }
     M* e = static_cast<M*>(lv.e);
