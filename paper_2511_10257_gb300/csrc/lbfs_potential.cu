@@ -290,6 +290,7 @@ __device__ __forceinline__ M coarse_at(const CaseParams& P, const M* e, int nx, 
 // restrict r - A e to the next level.  Up leg: add the bilinear prolongation of the
 // coarse correction, post-smooth, store e.
 constexpr int kFTX = 32, kFTY = 16, kFNu = 2;
+static_assert(kFTX == kFusedTX && kFTY == kFusedTY, "the host's tile lists use the same tile");
 constexpr int kHD = 2 * kFNu + 1, kHU = 2 * kFNu;
 
 template <int H>
