@@ -204,8 +204,9 @@ int64_t lbfs_last_launch_count(const lbfs_ctx* ctx);
  * for later steps and writes its id to *chosen (nullable).  ms (nullable, n entries)
  * receives the milliseconds per launch of each shape id < n.  Shapes: 0 32x8,
  * 1 32x16, 2 64x8, 3 16x16, 4 64x4, 5 16x16 and 6 32x8 with registers cut for a
- * third resident block per SM, 7 16x16 and 8 32x8 with registers cut for a fourth
- * (the cuts apply in mixed precision). */
+ * third resident block per SM, 7 16x16 and 8 32x8 with registers cut for a fourth,
+ * 9 16x16 and 10 32x8 with a fourth block of 256 threads instead of 288 (the cuts
+ * apply in mixed precision). */
 lbfs_status lbfs_autotune(lbfs_ctx* ctx, int32_t reps, int32_t* chosen, double* ms, int32_t n);
 
 /* Kernel timing.  While enabled, lbfs_step brackets every launch with CUDA events on

@@ -660,10 +660,12 @@ struct StageShape {
     }
 };
 
-template <class R, class HR, int TX, int TY, int MINB, bool HALF>
+// NT: threads per block (0: the shape's default, one thread per two faces)
+template <class R, class HR, int TX, int TY, int MINB, bool HALF, int NTB = 0>
 static cudaError_t launch_t(const DevCase* cases, const TileRef* tiles, int ntiles, int stage, cudaStream_t st) {
     using S = StageShape<TX, TY>;
-    auto kern = stage_kernel<R, HR, TX, TY, S::NT, MINB, HALF>;
+    constexpr int NT = NTB > 0 ? NTB : S::NT;
+    auto kern = stage_kernel<R, HR, TX, TY, NT, MINB, HALF>;
     static bool configured = false;
     const size_t sm = S::template smem<R>();
     if (!configured) {
@@ -674,17 +676,18 @@ static cudaError_t launch_t(const DevCase* cases, const TileRef* tiles, int ntil
         if (e != cudaSuccess) return e;
         configured = true;
     }
-    kern<<<ntiles, S::NT, sm, st>>>(cases, tiles, ntiles, stage);
+    kern<<<ntiles, NT, sm, st>>>(cases, tiles, ntiles, stage);
     return cudaGetLastError();
 }
 
 // Tile shapes the autotuner chooses from (id -> TX x TY cells per block, and the
 // number of blocks per SM the register budget is cut for in mixed precision: 1 for
-// ids 0-2, 2 for 3-4, 3 for 5-6, 4 for 7-8).  All have 256 or more cells, so a case
-// never has more stage tiles than with 16 x 16.
-static constexpr int kShapes = 9;
-static constexpr int kShapeW[kShapes] = {32, 32, 64, 16, 64, 16, 32, 16, 32};
-static constexpr int kShapeH[kShapes] = {8, 16, 8, 16, 4, 16, 8, 16, 8};
+// ids 0-2, 2 for 3-4, 3 for 5-6, 4 for 7-10).  Ids 9 and 10 run 256 threads (one per
+// cell) instead of 288, which leaves 64 registers a thread at four blocks per SM.  All
+// have 256 or more cells, so a case never has more stage tiles than with 16 x 16.
+static constexpr int kShapes = 11;
+static constexpr int kShapeW[kShapes] = {32, 32, 64, 16, 64, 16, 32, 16, 32, 16, 32};
+static constexpr int kShapeH[kShapes] = {8, 16, 8, 16, 4, 16, 8, 16, 8, 16, 8};
 
 int stage_tile_shapes() { return kShapes; }
 int stage_tile_w(int prec, int tile) {
@@ -696,12 +699,12 @@ int stage_tile_h(int prec, int tile) {
     return kShapeH[(tile >= 0 && tile < kShapes) ? tile : 0];
 }
 
-template <class R, int TX, int TY, int MINB>
+template <class R, int TX, int TY, int MINB, int NTB = 0>
 static cudaError_t launch_h(int half, const DevCase* cases, const TileRef* tiles, int ntiles, int stage,
                             cudaStream_t st) {
     using HR = typename HeStore<R>::T;
-    return half ? launch_t<R, HR, TX, TY, MINB, true>(cases, tiles, ntiles, stage, st)
-                : launch_t<R, HR, TX, TY, MINB, false>(cases, tiles, ntiles, stage, st);
+    return half ? launch_t<R, HR, TX, TY, MINB, true, NTB>(cases, tiles, ntiles, stage, st)
+                : launch_t<R, HR, TX, TY, MINB, false, NTB>(cases, tiles, ntiles, stage, st);
 }
 
 // MINB2/3/4: the blocks per SM of ids 3-4, 5-6 and 7-8 (all 1 in FP64, whose
@@ -718,6 +721,8 @@ static cudaError_t launch_prec(int tile, int half, const DevCase* cases, const T
     case 6: return launch_h<R, 32, 8, MINB3>(half, cases, tiles, ntiles, stage, st);
     case 7: return launch_h<R, 16, 16, MINB4>(half, cases, tiles, ntiles, stage, st);
     case 8: return launch_h<R, 32, 8, MINB4>(half, cases, tiles, ntiles, stage, st);
+    case 9: return launch_h<R, 16, 16, MINB4, 256>(half, cases, tiles, ntiles, stage, st);
+    case 10: return launch_h<R, 32, 8, MINB4, 256>(half, cases, tiles, ntiles, stage, st);
     default: return launch_h<R, 32, 8, 1>(half, cases, tiles, ntiles, stage, st);
     }
 }

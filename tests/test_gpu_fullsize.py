@@ -22,7 +22,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 STATE = [I.HE, I.P, I.C, I.MX, I.MY, I.FSPREV]
 CMP = [I.HE, I.P, I.C, I.MX, I.MY, I.T, I.FL]
 MARGIN = 12
-BENCH_TILE = 7   # the shape the autotuner keeps for these grids (16 x 16, four blocks per SM)
+BENCH_TILE = 9   # the shape the autotuner keeps for these grids (16 x 16, four blocks of 256 threads per SM)
 
 
 def _windows(nx, ny, R, angle):
