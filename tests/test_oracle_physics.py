@@ -326,3 +326,57 @@ def test_ferrofluid_drop_small_deformation():
     steady = cc + d2 * d2 / (d1 - d2)
     expect = chi * chi * bo / (3.0 * (2.0 + chi) ** 2)
     assert steady == pytest.approx(expect, rel=0.05)
+
+
+def _dense_potential(c, C):
+    """Eq. 4 on the five-point stencil assembled as a dense matrix and solved directly:
+    face coefficient the mean of the two cells' mu_m = 1 + chi(C) (all liquid or gas,
+    F_s = 0), a Dirichlet wall holding the far field phi_w = -H0 (x cos a + y sin a) at
+    the wall face half a cell from the centre, an insulating wall carrying no flux."""
+    ny, nx = C.shape
+    mu = 1.0 + (c["chi_g"] + C * (c["chi_l"] - c["chi_g"]))
+    a = math.radians(c["field_angle_deg"])
+    far = lambda x, y: -c["H0"] * (x * math.cos(a) + y * math.sin(a))
+    n = nx * ny
+    A = np.zeros((n, n))
+    b = np.zeros(n)
+    for j in range(ny):
+        for i in range(nx):
+            k = j * nx + i
+            for di, dj, wall in ((-1, 0, 0), (1, 0, 1), (0, -1, 2), (0, 1, 3)):
+                ii, jj = i + di, j + dj
+                periodic = c["periodic_x"] if di else c["periodic_y"]
+                if 0 <= ii < nx and 0 <= jj < ny or periodic:
+                    ii, jj = ii % nx, jj % ny
+                    mf = 0.5 * (mu[j, i] + mu[jj, ii])
+                    A[k, k] += mf
+                    A[k, jj * nx + ii] -= mf
+                elif not (c["mag_bc"] == 1 and wall < 2):
+                    x = 0.0 if wall == 0 else (nx if wall == 1 else i + 0.5)
+                    y = 0.0 if wall == 2 else (ny if wall == 3 else j + 0.5)
+                    A[k, k] += 2.0 * mu[j, i]
+                    b[k] += 2.0 * mu[j, i] * far(x, y)
+    return np.linalg.solve(A, b).reshape(ny, nx)
+
+
+@pytest.mark.parametrize("kw", [dict(), dict(mag_bc=1, field_angle_deg=90.0), dict(periodic_x=1),
+                                dict(field_angle_deg=0.0)])
+def test_potential_matches_dense_solve(kw):
+    """the oracle's iterative potential solve against a dense direct solve of Eq. 4 on a
+    12x10 grid with a smooth random C (chi_l = 2), to 1e-11 of the field's scale"""
+    args = dict(init=2, T_init=1.0, stefan=0.0, latent=10.0, chi_l=2.0, chi_s=2.0, chi_g=0.0,
+                H0=0.05, bo_m=0.0, field_angle_deg=30.0)
+    args.update(kw)
+    c = I.case(12, 10, **args)
+    o = oracle.Oracle(c)
+    rng = np.random.default_rng(3)
+    X, Y = np.meshgrid(np.arange(12) + 0.5, np.arange(10) + 0.5)
+    C = np.clip(0.5 + 0.6 * np.sin(0.5 * X + rng.uniform(0, 6)) * np.cos(0.4 * Y + rng.uniform(0, 6)), 0, 1)
+    o.set(I.C, C)
+    cp = C * c["cp_l"] + (1 - C) * c["cp_g"]
+    o.set(I.HE, cp * 1.0 + c["latent"])       # T = 1 everywhere: no solid, F_s = 0
+    assert np.all(o.get(I.FL) == 1.0)
+    assert o.solve_potential() == 0
+    phi = o.get(I.PHI)
+    ref = _dense_potential(c, C)
+    assert np.max(np.abs(phi - ref)) <= 1e-11 * np.max(np.abs(ref))
