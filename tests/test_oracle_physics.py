@@ -380,3 +380,28 @@ def test_potential_matches_dense_solve(kw):
     phi = o.get(I.PHI)
     ref = _dense_potential(c, C)
     assert np.max(np.abs(phi - ref)) <= 1e-11 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("angle,N", [(0.0, 1.0 / 3.0), (90.0, 2.0 / 3.0)])
+def test_elliptic_inclusion_field(angle, N):
+    """A diffuse elliptic cylinder (semi-axes a = 30 along x, b = 15 along y) of
+    susceptibility chi = 1 in a uniform far field along a principal axis: the interior
+    field is uniform, |H_in| = H0 / (1 + chi N) with the demagnetising factor
+    N = b/(a + b) along x and a/(a + b) along y.  Diffuse-interface bound as for the disk."""
+    n, a, b, chi, H0 = 256, 30.0, 15.0, 1.0, 0.01
+    c = I.case(n, n, init=2, T_init=1.0, stefan=0.0, latent=10.0, H0=H0, bo_m=0.0, field_angle_deg=angle,
+               chi_l=chi, chi_s=chi, chi_g=0.0)
+    o = oracle.Oracle(c)
+    X, Y = np.meshgrid(np.arange(n) + 0.5 - n / 2, np.arange(n) + 0.5 - n / 2)
+    g = np.sqrt((X / a) ** 2 + (Y / b) ** 2)
+    grad = np.sqrt((X / a ** 2) ** 2 + (Y / b ** 2) ** 2) / np.maximum(g, 1e-12)
+    d = (1.0 - g) / np.maximum(grad, 1e-12)          # signed distance to the ellipse, first order
+    o.set(I.C, 0.5 + 0.5 * np.tanh(2.0 * d / c["xi"]))
+    assert o.solve_potential() == 0
+    phi = o.get(I.PHI)
+    m = n // 2
+    Hx = -(phi[m - 4:m + 4, m - 7:m + 9] - phi[m - 4:m + 4, m - 9:m + 7]) / 2
+    Hy = -(phi[m - 3:m + 5, m - 8:m + 8] - phi[m - 5:m + 3, m - 8:m + 8]) / 2
+    H = np.hypot(Hx, Hy)
+    assert H.mean() == pytest.approx(H0 / (1.0 + chi * N), rel=0.03)
+    assert H.std() < 0.01 * H.mean()
