@@ -34,8 +34,8 @@ FALLBACK_HBM_GBS = 6800.0
 
 # algorithmic bytes per cell of one stage launch, averaged over the three stages:
 # stage 1 reads W^n, F_s^{n-1}, phi and writes W^1; stages 2 and 3 also read W^n
-# cell-locally; stage 3 also writes F_s^n and mu_m.  W is H_e (FP64) plus p, m_x,
-# m_y, C in the working precision.
+# cell-locally; stage 3 also writes F_s^n and mu_m.  W is H_e (8 bytes: FP64, or an
+# FP32 pair in mixed precision) plus p, m_x, m_y, C in the working precision.
 def stage_bytes_per_cell(prec: int) -> float:
     r = 8 if prec == 0 else 4
     w = 8 + 4 * r
@@ -84,12 +84,16 @@ def reduce_over_ranks(elapsed_s: float, units: float, world: int):
 
 
 def stage_source_hash() -> str:
-    """hash of the stage kernel's sources: profiled counters apply only to this version"""
+    """hash of the stage kernel's code (comments and blank lines left out): profiled
+    counters apply only to this version"""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("lbfs_stage.cu", "lbfs_internal.cuh"):
-        with open(os.path.join(ROOT, "paper_2511_10257_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2511_10257_gb300", "csrc", f)) as fh:
+            src = re.sub(r"/\*.*?\*/", "", fh.read(), flags=re.S)
+        lines = [re.sub(r"//.*", "", ln).rstrip() for ln in src.splitlines()]
+        h.update("\n".join(ln for ln in lines if ln).encode())
     return h.hexdigest()[:16]
 
 

@@ -43,9 +43,10 @@ typedef enum {
 
 typedef enum {
     LBFS_FP64 = 0,   /* every field and flux in FP64                                      */
-    LBFS_MIXED = 1   /* fluxes, forces and state in FP32 except H_e (FP64 storage and
-                        FP64 enthalpy inversion); potential by FP32 multigrid inside
-                        FP64 residual refinement; FP64 global sums                        */
+    LBFS_MIXED = 1   /* fluxes, forces and state in FP32 except H_e, which is stored,
+                        updated and inverted (Eq. 8 thresholds) as an FP32 pair of about
+                        48 significant bits; potential by FP32 multigrid inside
+                        FP64-accurate residual refinement; FP64-accurate global sums     */
 } lbfs_precision;
 
 /* Context configuration.  Zero-initialise and set what you need. */

@@ -147,8 +147,10 @@ __device__ __forceinline__ R mix(R Fs, R C, R gs, R gl, R gg) {
 }
 
 // Eq. 8 as above with the two threshold differences H_e - H_es and H_e - H_el formed
-// in the enthalpy's precision H (FP64 storage in both modes) and everything after
-// them in R.  Hes_h = C_p,s T_m and L_h = L are given in H.
+// in precision H and everything after them in R.  Hes_h = C_p,s T_m and L_h = L are
+// given in H.  Used with H = R (the interface enthalpy in the face fluxes) and with
+// H = R = double (the stored enthalpy in FP64 mode); the mixed-precision stored
+// enthalpy, an FP32 pair, goes through invert_hp.
 template <class R, class H>
 __device__ __forceinline__ void invert_h(const PhysT<R>& Q, H Hes_h, H L_h, H He, R C, R& T, R& Fl,
                                          R* He_r = nullptr) {
