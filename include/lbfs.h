@@ -138,8 +138,11 @@ enum {
     LBFS_FIELD_FSPREV = 12 /* solid fraction of the previous step           */
 };
 
-/* Create a context on cfg->device.  Returns LBFS_EINVAL for a bad config, LBFS_ECUDA
- * if the device cannot be used.  *out is NULL on failure. */
+/* Create a context on cfg->device (bookkeeping; no counterpart in the paper).  The
+ * context owns its device memory and, unless cfg->cuda_stream is given (borrowed, not
+ * destroyed), its stream.  Returns LBFS_EINVAL for a bad config, LBFS_ECUDA if the
+ * device cannot be used, LBFS_ENOMEM if its tables cannot be allocated.  *out is NULL
+ * on failure. */
 lbfs_status lbfs_create(const lbfs_config* cfg, lbfs_ctx** out);
 
 /* (Re)define case slot case_id (0 <= case_id < max_cases) and initialise its fields on
@@ -149,16 +152,33 @@ lbfs_status lbfs_create(const lbfs_config* cfg, lbfs_ctx** out);
  * the explicit diffusion limit) before any allocation; LBFS_EINVAL on failure. */
 lbfs_status lbfs_set_case(lbfs_ctx* ctx, int32_t case_id, const lbfs_case_desc* desc);
 
-/* Overwrite stored fields of a case from host FP64 arrays (layout as lbfs_fields).
- * Settable: PHI, HE, P, C, MX, MY, FSPREV.  Other bits give LBFS_EINVAL. */
+/* Overwrite stored fields of a case from host FP64 arrays: the evolved state of Eq. 39
+ * (H_e, p, rho c_s^2 u, rho c_s^2 v, C), the potential phi and the previous step's F_s
+ * (R13).  Layout as lbfs_fields: one nx*ny row-major array (x fastest) per set bit, in
+ * increasing id order; host_in is caller-owned and only read.  Settable: PHI, HE, P,
+ * C, MX, MY, FSPREV; other bits, an empty mask, a NULL buffer or an undefined case give
+ * LBFS_EINVAL.  The statistics are recomputed from the imported state and the next
+ * step re-converges the potential. */
 lbfs_status lbfs_set_fields(lbfs_ctx* ctx, int32_t case_id, uint32_t mask, const double* host_in);
 
-/* Advance every defined case by nsteps time steps on the context's stream and wait
- * for completion.  out (nullable) receives max_cases stats (undefined slots zero).
- * LBFS_EDIVERGED / LBFS_ENOTCONVERGED are reported after the steps ran. */
+/* Advance every defined case by nsteps time steps (Table 1, Sec. 3.4): per step the
+ * lagged solid-fraction rate, the magnetic potential of Eq. 4 (multigrid, to the
+ * context's tolerance), then three SSP-RK3 stages of the LBFS finite-volume update
+ * (reconstruction Eq. 44, interface values Eq. 45, equilibria Eqs. 20, 28, 29,
+ * starred distributions Eqs. 16, 22, 32, 33, fluxes Eq. 43, sources Eqs. 6, 41,
+ * finite-volume sum Eq. 42, Eq. 8 inversion), the solid held at rest, and the Eq. 51
+ * statistics.  Runs on the context's stream and waits for completion.  out (nullable,
+ * caller-owned, max_cases entries) receives each slot's statistics (undefined slots
+ * zero).  nsteps < 0 gives LBFS_EINVAL before any launch; LBFS_EDIVERGED (a non-finite
+ * value) and LBFS_ENOTCONVERGED (the potential missed its tolerance) are reported after
+ * the steps ran, with the stats still filled. */
 lbfs_status lbfs_step(lbfs_ctx* ctx, int32_t nsteps, lbfs_case_stats* out);
 
-/* Copy fields of a case to caller-owned host memory (FP64, see field ids). */
+/* Copy fields of a case to caller-owned host memory: nx*ny FP64 values per set bit of
+ * mask, row-major (x fastest), in increasing id order.  Derived fields are evaluated
+ * from the stored state: T and F_l by Eq. 8, rho by Eq. 11, u and v from the momentum,
+ * mu_c = 2 beta C (C-1)(2C-1) - kappa lap C (with the wall ghost rule).  An empty or
+ * unknown mask, a NULL buffer or an undefined case give LBFS_EINVAL. */
 lbfs_status lbfs_fields(lbfs_ctx* ctx, int32_t case_id, uint32_t mask, double* host_out);
 
 /* Sec. 5 diagnostics of a case's current state (lattice units, FP64 arithmetic). */
@@ -194,29 +214,31 @@ lbfs_status lbfs_diagnostics(lbfs_ctx* ctx, int32_t case_id, lbfs_case_diag* out
  * completion. */
 lbfs_status lbfs_potential_pseudo_time(lbfs_ctx* ctx, int32_t case_id, int32_t iters, double dtau);
 
-/* Number of device kernel launches the last lbfs_step issued (graph nodes count). */
+/* Number of device kernel launches the last lbfs_step issued (graph nodes count);
+ * bookkeeping, no counterpart in the paper. */
 int64_t lbfs_last_launch_count(const lbfs_ctx* ctx);
 
-/* Autotuner of the stage kernel's tile shape (the tile is the block's share of the
- * grid; the halo is fixed at three cells by the stencil).  Times `reps` launches of
- * each compiled tile shape on the context's current cases (Runge-Kutta stage 2,
- * which writes only a stage buffer, so the state is untouched), keeps the fastest
- * (a shape with a higher id must be more than 2 % faster than the best before it)
- * for later steps and writes its id to *chosen (nullable).  ms (nullable, n entries)
- * receives the milliseconds per launch of each shape id < n.  Shapes: 0 32x8,
- * 1 32x16, 2 64x8, 3 16x16, 4 64x4, 5 16x16 and 6 32x8 with registers cut for a
- * third resident block per SM, 7 16x16 and 8 32x8 with registers cut for a fourth,
- * 9 16x16 and 10 32x8 with a fourth block of 256 threads instead of 288 (the cuts
- * apply in mixed precision). */
+/* Autotuner of the stage kernel's tile shape (no counterpart in the paper).  The tile
+ * is a block's share of the grid; the halo is fixed at three cells by the stencil.
+ * Times `reps` launches of each compiled tile shape on the context's current cases
+ * (Runge-Kutta stage 2, which writes only a stage buffer, so the state is untouched),
+ * keeps the fastest (a shape with a higher id must be more than 2 % faster than the
+ * best before it) for later steps and writes its id to *chosen (nullable).  ms
+ * (nullable, n entries) receives the milliseconds per launch of each shape id < n.
+ * Shapes: 0 32x8, 1 32x16, 2 64x8, 3 16x16, 4 64x4, 5 16x16 and 6 32x8 with registers
+ * cut for a third resident block per SM, 7 16x16 and 8 32x8 with registers cut for a
+ * fourth, 9 16x16 and 10 32x8 with a fourth block of 256 threads instead of 288 (the
+ * cuts apply in mixed precision).  LBFS_EINVAL without a defined case or for reps < 1. */
 lbfs_status lbfs_autotune(lbfs_ctx* ctx, int32_t reps, int32_t* chosen, double* ms, int32_t n);
 
-/* Kernel timing.  While enabled, lbfs_step brackets every launch with CUDA events on
- * the context's stream and accumulates the elapsed device time per kernel class:
- * LBFS_TIMING_STAGE (the fused Runge-Kutta stage kernel), LBFS_TIMING_POTENTIAL (the
- * whole potential solve of a step), LBFS_TIMING_FINALIZE (step-end statistics).
- * Enabling clears the accumulators; while enabled the step is never replayed from a
- * graph.  lbfs_timing_read copies n (<= 3) accumulated milliseconds and event-pair
- * counts into caller-owned arrays (either may be NULL). */
+/* Kernel timing (no counterpart in the paper).  While enabled, lbfs_step brackets
+ * every launch with CUDA events on the context's stream and accumulates the elapsed
+ * device time per kernel class: LBFS_TIMING_STAGE (the fused Runge-Kutta stage
+ * kernel), LBFS_TIMING_POTENTIAL (the whole potential solve of a step),
+ * LBFS_TIMING_FINALIZE (step-end statistics).  Enabling clears the accumulators; while
+ * enabled the step is never replayed from a graph.  lbfs_timing_read copies n (<= 3)
+ * accumulated milliseconds and event-pair counts into caller-owned arrays (either may
+ * be NULL). */
 enum { LBFS_TIMING_STAGE = 0, LBFS_TIMING_POTENTIAL = 1, LBFS_TIMING_FINALIZE = 2 };
 lbfs_status lbfs_timing(lbfs_ctx* ctx, int32_t enable);
 lbfs_status lbfs_timing_read(lbfs_ctx* ctx, double* ms, int64_t* counts, int32_t n);
@@ -244,10 +266,12 @@ lbfs_status lbfs_timing_read(lbfs_ctx* ctx, double* ms, int64_t* counts, int32_t
 lbfs_status lbfs_state_stats_noalloc(const lbfs_case_desc* desc, const double* d_He, const double* d_C,
                                      double* d_out, void* stream, char* err, size_t err_len);
 
-/* Release all device memory and the owned stream (if any). */
+/* Release all device memory and the owned stream (if any); a borrowed stream is left
+ * alone.  NULL is ignored.  Bookkeeping, no counterpart in the paper. */
 void lbfs_destroy(lbfs_ctx* ctx);
 
-/* Sticky message of the last failure on ctx ("" if none); valid until the next call. */
+/* Sticky message of the last failure on ctx ("" if none); valid until the next call
+ * on ctx.  Bookkeeping, no counterpart in the paper. */
 const char* lbfs_last_error(const lbfs_ctx* ctx);
 
 #ifdef __cplusplus
