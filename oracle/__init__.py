@@ -71,6 +71,12 @@ class OracleDiag(ct.Structure):
 FLAG_LITERAL_FSTAR_SIGN = 1
 FLAG_LITERAL_MUC_SIGN = 2
 FLAG_KEEP_POTENTIAL = 4
+# planted mistakes, for showing that a pin catches them (tests only)
+FLAG_PLANT_VOLUME_SIGN = 8
+FLAG_PLANT_GRAVITY_SIGN = 16
+FLAG_PLANT_WALL_SIDE = 32
+FLAG_PLANT_WALL_FULL = 64
+FLAG_PLANT_IBM_SIGN = 128
 
 _lib = None
 

@@ -389,7 +389,9 @@ static void wall_face(oracle_state* s, int wall, int i, int j, double out[5])
     double lam = oracle_mix(Fs, C, c->lam_s, c->lam_l, c->lam_g);
     double side = (wall == 0 || wall == 2) ? 1.0 : -1.0; /* +1: inner cell lies at +axis */
     double ut = (wall < 2) ? s->q[Q_V][g] : s->q[Q_U][g];
-    double dut = side * ut / 0.5;
+    double dn = (c->flags & ORACLE_FLAG_PLANT_WALL_FULL) ? 1.0 : 0.5; /* wall to inner centre */
+    double sside = (c->flags & ORACLE_FLAG_PLANT_WALL_SIDE) ? -side : side;
+    double dut = sside * ut / dn;
     double T = s->q[Q_T][g];
     double dT = side * (T - c->wall_T[wall]) / 0.5;
     for (int n = 0; n < 5; ++n) out[n] = 0.0;
@@ -479,12 +481,15 @@ static void compute_rhs(oracle_state* s, double* const* W, double* R)
             double dHy = 0.5 * (s->H2[GI(s, i, j + 1)] - s->H2[GI(s, i, j - 1)]);
             double dmx = s->gx[Q_MUC][k], dmy = s->gy[Q_MUC][k];
             double Sd = s->Sdot[k];
+            double vr = (c->flags & ORACLE_FLAG_PLANT_VOLUME_SIGN) ? -s->vol_ratio : s->vol_ratio;
+            double grav = (c->flags & ORACLE_FLAG_PLANT_GRAVITY_SIGN) ? -c->gravity : c->gravity;
+            double ibm = (c->flags & ORACLE_FLAG_PLANT_IBM_SIGN) ? 1.0 : -1.0;
             double src[5];
             src[W_HE] = cp * T * divu;
-            src[W_P] = u * CS2 * drx + v * CS2 * dry + rho * CS2 * s->vol_ratio * Sd;
-            src[W_MX] = CS2 * (-C * dmx + 0.5 * chi * dHx - rho * u * Sd);
-            src[W_MY] = CS2 * (-C * dmy + 0.5 * chi * dHy + rho * c->gravity - rho * v * Sd);
-            src[W_C] = C * s->vol_ratio * Sd;
+            src[W_P] = u * CS2 * drx + v * CS2 * dry + rho * CS2 * vr * Sd;
+            src[W_MX] = CS2 * (-C * dmx + 0.5 * chi * dHx + ibm * rho * u * Sd);
+            src[W_MY] = CS2 * (-C * dmy + 0.5 * chi * dHy + rho * grav + ibm * rho * v * Sd);
+            src[W_C] = C * vr * Sd;
             for (int n = 0; n < 5; ++n)
                 R[n * N + k] = -(fr[n] - fl[n]) - (ft[n] - fb[n]) + src[n];
         }

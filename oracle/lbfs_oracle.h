@@ -60,6 +60,13 @@ typedef struct oracle_case {
 /* Keep the potential that was set instead of solving it at the start of a step: lets
  * a test advance a window of a larger grid with that grid's solved potential. */
 #define ORACLE_FLAG_KEEP_POTENTIAL      4
+/* Planted mistakes: each flips or rescales one term of the step so that a test can
+ * show that the pin on that term fails.  Never set outside those tests. */
+#define ORACLE_FLAG_PLANT_VOLUME_SIGN   8   /* (rho_s/rho_l - 1) for (1 - rho_s/rho_l)   */
+#define ORACLE_FLAG_PLANT_GRAVITY_SIGN  16  /* F_g = -rho g                               */
+#define ORACLE_FLAG_PLANT_WALL_SIDE     32  /* wall shear du_t/dn taken towards the wall  */
+#define ORACLE_FLAG_PLANT_WALL_FULL     64  /* the wall a full cell from the inner centre */
+#define ORACLE_FLAG_PLANT_IBM_SIGN      128 /* F_IBM = +rho u dF_s/dt                      */
 
 /* Field identifiers (same numbering as the library's field mask bits). */
 enum { OF_PHI = 0, OF_HE, OF_T, OF_FL, OF_P, OF_U, OF_V, OF_C, OF_MUC, OF_RHO,
