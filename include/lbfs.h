@@ -248,7 +248,7 @@ lbfs_status lbfs_timing_read(lbfs_ctx* ctx, double* ms, int64_t* counts, int32_t
  * cannot allocate device memory, e.g. code running inside another component's fixed
  * memory pool or while that component records work, which must not call cudaMalloc).
  *   desc:  the case; only nx, ny, cp_l, cp_g, cp_s, T_m, stefan/latent and wall_T[2]
- *          are read (the Eq. 8 inversion).
+ *          are read (the enthalpy inversion the step uses).
  *   d_He, d_C: device arrays of nx*ny FP64 values, row-major with x fastest (caller-owned).
  *   d_out: device array of 5 FP64 values (caller-owned) receiving sum C, sum H_e,
  *          sum F_l over droplet cells (C >= 1/2), the number of droplet cells and Q_L.
@@ -259,8 +259,10 @@ lbfs_status lbfs_timing_read(lbfs_ctx* ctx, double* ms, int64_t* counts, int32_t
  * (640 KiB) that every device using this library keeps until the process exits;
  * ny > 16384 returns LBFS_EINVAL before any launch.  No cudaMalloc, cudaFree or other
  * allocating call is made.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first call before
- * any stream capture.  All calls share the array and every call rewrites the rows it
+ * address (cudaGetSymbolAddress) with that device current and keeps it for the life of
+ * the process; make that first call before any stream capture.  A cudaDeviceReset
+ * reloads the module, which leaves the kept address stale, so a process that resets a
+ * device must not call this again afterwards.  All calls share the array and every call rewrites the rows it
  * uses, so nothing needs clearing, but calls whose kernels overlap on the GPU (other
  * streams, other host threads) race on it: order them on one stream. */
 lbfs_status lbfs_state_stats_noalloc(const lbfs_case_desc* desc, const double* d_He, const double* d_C,

@@ -506,6 +506,7 @@ lbfs_status lbfs_set_case(lbfs_ctx* ctx, int32_t id, const lbfs_case_desc* desc)
     CaseParams P;
     r = resolve(ctx, *desc, P);
     if (r != LBFS_OK) return r;
+    CK(cudaSetDevice(ctx->cfg.device));
     // multigrid hierarchy
     DevCase hd;
     std::memset(&hd, 0, sizeof(hd));
@@ -620,6 +621,7 @@ lbfs_status lbfs_set_fields(lbfs_ctx* ctx, int32_t id, uint32_t mask, const doub
                               (1u << LBFS_FIELD_C) | (1u << LBFS_FIELD_MX) | (1u << LBFS_FIELD_MY) |
                               (1u << LBFS_FIELD_FSPREV);
     if ((mask & ~settable) || mask == 0 || !host_in) return fail(ctx, LBFS_EINVAL, "bad field mask or buffer");
+    CK(cudaSetDevice(ctx->cfg.device));
     const int nf = __builtin_popcount(mask);
     const size_t N = (size_t)s.hd.P.nx * s.hd.P.ny;
     r = ensure_scratch(ctx, nf * N * sizeof(double));
@@ -640,6 +642,7 @@ lbfs_status lbfs_fields(lbfs_ctx* ctx, int32_t id, uint32_t mask, double* host_o
     Slot& s = ctx->slots[id];
     if (!s.defined) return fail(ctx, LBFS_EINVAL, "case not defined");
     if (mask == 0 || (mask >> 13) || !host_out) return fail(ctx, LBFS_EINVAL, "bad field mask or buffer");
+    CK(cudaSetDevice(ctx->cfg.device));
     const int nf = __builtin_popcount(mask);
     const size_t N = (size_t)s.hd.P.nx * s.hd.P.ny;
     r = ensure_scratch(ctx, nf * N * sizeof(double));

@@ -35,7 +35,8 @@ void set_msg(char* buf, size_t len, const char* msg) {
     }
 }
 
-// Device address of the scratch on the current device, looked up once per device.
+// Device address of the scratch on the current device, looked up once per device and
+// kept for the life of the process (a cudaDeviceReset would make it stale).
 cudaError_t scratch_on(int dev, double** out) {
     std::lock_guard<std::mutex> lk(g_mu);
     if (!g_addr[dev]) {

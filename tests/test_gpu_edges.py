@@ -79,3 +79,28 @@ def test_arguments_are_checked():
     assert L.lbfs_fields(h, 0, 1 << I.C, ptr) == 0                  # the context is still usable
     s.step(1)
     s.close()
+
+
+def test_calls_select_the_context_device():
+    """set_case, set_fields and fields run on the context's device even when another
+    device is current in the calling thread."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.device_count() < 2:
+        pytest.skip("needs two devices")
+    c = I.case(32, 16, radius=6.0, bo_m=1.0)
+    s = lbfs.Solver(precision=lbfs.FP64, max_cases=1, device=0)
+    torch.cuda.set_device(1)
+    try:
+        s.set_case(0, c)
+        st = I.random_state(32, 16, seed=3)
+        s.set_fields(0, st)
+        s.step(3)
+        got = s.fields(0, [I.C, I.HE])
+    finally:
+        torch.cuda.set_device(0)
+        s.close()
+    ref = oracle.Oracle(c)
+    ref.set_state(st)
+    ref.step(3)
+    for f in (I.C, I.HE):
+        assert np.max(np.abs(got[f] - ref.get(f))) <= 1e-9 * np.max(np.abs(ref.get(f)))
