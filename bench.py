@@ -296,7 +296,7 @@ def run_gpu(args):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     barrier()
     ev0.record(stream)
-    solver.step(args.steps)
+    timed_stats = solver.step(args.steps)
     ev1.record(stream)
     barrier()
     elapsed = ev0.elapsed_time(ev1) / 1e3
@@ -320,7 +320,9 @@ def run_gpu(args):
             hosts.append(host)
             outs.append(torch.empty((len(out_ids), c["ny"], c["nx"]), dtype=torch.float64,
                                     pin_memory=True).numpy())
-        stats_bytes = 80 * len(cases)
+        stats_bytes = 88 * len(cases)   # one lbfs_case_stats per case
+        # one untimed step records and instantiates the step graph the job replays
+        solver.step(1)
         barrier()
         t0 = time.perf_counter()
         for k, host in enumerate(hosts):
@@ -347,15 +349,26 @@ def run_gpu(args):
             s64.set_case(k, c)
         s64.step(2)
         barrier()
+        # eager launches with per-kernel-class events, so the step splits into stage,
+        # potential and step-end time
+        s64.timing(True)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        s64.step(args.fp64_steps)
+        st64 = s64.step(args.fp64_steps)
         b.record(stream)
         barrier()
         t64 = a.elapsed_time(b) / 1e3
+        (s_ms, s_n), (p_ms, p_n), (f_ms, f_n) = s64.timing_read()
+        s64.timing(False)
         s64.close()
         fp64 = {"value": ncell * args.fp64_steps / t64 / 1e6, "unit": UNIT, "steps": args.fp64_steps,
-                "ms_per_step": 1e3 * t64 / args.fp64_steps}
+                "ms_per_step": 1e3 * t64 / args.fp64_steps,
+                "stage_ms_per_launch": s_ms / max(s_n, 1),
+                "stage_bytes_per_cell": stage_bytes_per_cell(lbfs.FP64),
+                "potential_ms_per_step": p_ms / max(p_n, 1),
+                "finalize_ms_per_step": f_ms / max(f_n, 1),
+                "pot_resid_max": max(x["pot_resid_max"] for x in st64),
+                "pot_cycles_mean": sum(x["pot_cycles_mean"] for x in st64) / len(st64)}
 
     if rank != 0:
         solver.close()
@@ -381,6 +394,11 @@ def run_gpu(args):
                 "launch_ms": stage_avg_s * 1e3, "issue": issue,
                 "potential_ms_per_step": pot_ms / max(pot_n, 1),
                 "finalize_ms_per_step": fin_ms / max(fin_n, 1)}
+    # the potential solve of every timed step, after its last cycle
+    potential = {"tol": solver.mg_tol_used(),
+                 "resid_max": max(x["pot_resid_max"] for x in timed_stats),
+                 "cycles_mean": sum(x["pot_cycles_mean"] for x in timed_stats) / len(timed_stats),
+                 "all_converged": all(x["pot_resid_max"] <= solver.mg_tol_used() for x in timed_stats)}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -411,6 +429,7 @@ def run_gpu(args):
                          f"(three state sets of {state_bytes / 2**20:.0f} MiB) against 129 MiB of L2, no flush"
                    if 3 * state_bytes > L2_BYTES else "working set fits L2 (no flush)"},
         "roofline": roofline,
+        "potential": potential,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

@@ -59,14 +59,19 @@ typedef struct lbfs_config {
     void* (*dev_alloc)(size_t bytes, void* user);  /* optional device allocator, e.g. a   */
     void  (*dev_free)(void* ptr, void* user);      /* framework's caching allocator       */
     void*   alloc_user;
-    int32_t mg_max_cycles;   /* potential refinement cycles per step (0: 40)                 */
-    double  mg_tol;          /* relative residual ||b - A phi|| / ||b|| (0: 1e-13 FP64,
-                                1e-6 mixed).  FP64 steps and the first mixed step after a
-                                state is set iterate to it; later mixed steps run at most
-                                one refinement cycle, skipped on the device when the
-                                residual already meets it                                  */
+    int32_t mg_max_cycles;   /* refinement cycles of a potential solve after a state is set,
+                                checked on the host (0: 40)                                */
+    double  mg_tol;          /* relative residual ||b - A phi|| / ||b|| every solve must
+                                reach (0: 1e-13 FP64, 1e-6 mixed)                          */
     int32_t tile;            /* stage-kernel tile shape id (see lbfs_autotune); 0: 32 x 8   */
-    int32_t reserved[7];
+    int32_t mg_warm_cycles;  /* refinement cycles available to the potential solve of each
+                                later step (0: 12 FP64, 3 mixed).  Each cycle ends with the
+                                residual of the corrected potential; once it meets mg_tol
+                                the case's remaining kernels return at once, on the device,
+                                so these steps need no host round trip and can be replayed
+                                as a CUDA graph.  A residual still above mg_tol after the
+                                last cycle makes lbfs_step return LBFS_ENOTCONVERGED     */
+    int32_t reserved[6];
 } lbfs_config;
 
 /* One case.  Walls are numbered 0 left (x = 0), 1 right (x = nx), 2 bottom (y = 0),
@@ -114,9 +119,11 @@ typedef struct lbfs_case_stats {
     double  Q_L;          /* Eq. 51: mean solid fraction of the droplet cells             */
     double  t;            /* simulated time                                               */
     double  t_freeze;     /* first t with Q_L >= 0.99 (linear in time); < 0 if not yet    */
-    double  pot_resid;    /* relative residual of the last potential solve                */
+    double  pot_resid;    /* relative residual after the last potential solve             */
     int32_t pot_cycles;   /* refinement cycles of the last potential solve                */
     int32_t nonfinite;    /* 1 if a non-finite value appeared                             */
+    double  pot_resid_max;   /* largest relative residual after a solve, over this call's steps */
+    double  pot_cycles_mean; /* mean refinement cycles per step over this call's steps       */
 } lbfs_case_stats;
 
 /* Field identifiers; a field mask is a bit set of (1u << id).  lbfs_fields returns

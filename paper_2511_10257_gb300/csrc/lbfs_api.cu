@@ -60,13 +60,19 @@ struct lbfs_ctx {
     int64_t launches = 0;
     double mg_tol = 0.0;
     int mg_max_cycles = 0;
+    int mg_warm_cycles = 0;
     int half = 0;          // every defined case has dts = 1/2
     int tile = 0;          // stage-kernel tile shape id (config or autotuner)
     bool pot_fresh = true; // a state was set since the last full potential solve
     cudaGraphExec_t gexec = nullptr;
     cudaGraph_t graph = nullptr;
-    int64_t graph_launches = 0;       // kernel nodes in one recorded step
+    int64_t graph_launches = 0;       // kernel nodes in one recorded step, the cycle body's aside
     cudaStream_t cap_stream = nullptr; // private stream used to record the graph
+    cudaStream_t body_stream = nullptr; // private stream used to record a conditional loop body
+    bool capturing = false;           // launches are being recorded into a graph
+    cudaGraphExec_t pot_exec = nullptr; // the warm potential solve as a graph, for eager steps
+    cudaGraph_t pot_graph = nullptr;
+    int64_t cycle_launches = 0;       // kernels of one refinement cycle
     // kernel timing (events on the context stream)
     bool timing = false;
     double t_ms[3] = {0, 0, 0};
@@ -109,8 +115,12 @@ void dfree(lbfs_ctx* ctx, void* p) {
 void drop_graph(lbfs_ctx* ctx) {
     if (ctx->gexec) cudaGraphExecDestroy(ctx->gexec);
     if (ctx->graph) cudaGraphDestroy(ctx->graph);
+    if (ctx->pot_exec) cudaGraphExecDestroy(ctx->pot_exec);
+    if (ctx->pot_graph) cudaGraphDestroy(ctx->pot_graph);
     ctx->gexec = nullptr;
     ctx->graph = nullptr;
+    ctx->pot_exec = nullptr;
+    ctx->pot_graph = nullptr;
 }
 
 cudaEvent_t take_event(lbfs_ctx* ctx) {
@@ -355,29 +365,116 @@ lbfs_status vcycle(lbfs_ctx* ctx) {
     return LBFS_OK;
 }
 
-// The potential of the current state.  A full solve (host-checked refinement cycles
-// until every case meets mg_tol) runs in FP64 mode and, in mixed mode, after a
-// state was set.  A warm mixed step runs one refinement cycle with no host round
-// trip: the residual's norm sets a per-case flag on the device and the V-cycle and
-// correction kernels skip converged cases.
+// The warm potential solve, recorded into the graph being captured on ctx->stream:
+// the step's first residual and check, then a conditional WHILE node whose body is one
+// refinement cycle (V-cycle, correction, residual of the corrected potential, check).
+// The checks decide on the device whether the body runs again, so a step whose warm
+// start already meets mg_tol runs no cycle at all, and a step never runs more than
+// mg_warm_cycles.
+lbfs_status capture_warm_potential(lbfs_ctx* ctx) {
+    const int p = ctx->prec, K = ctx->mg_warm_cycles;
+    cudaStream_t s = ctx->stream;
+    int* nd = ctx->d_flag + 1;
+    unsigned* ticket = reinterpret_cast<unsigned*>(ctx->d_flag + 2);
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, nullptr, nullptr, nullptr));
+    if (cs != cudaStreamCaptureStatusActive || !g) return fail(ctx, LBFS_ECUDA, "potential capture is not active");
+    cudaGraphConditionalHandle h;
+    CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    LK(launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], 1, s));
+    LK(launch_mg_finalize(p, ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, 1, K, nd, ticket, h, 1, s));
+    const cudaGraphNode_t* deps = nullptr;
+    size_t ndeps = 0;
+    CK(cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, nullptr, &ndeps));
+    // (the node-parameter type has no default constructor: zeroed storage)
+    alignas(cudaGraphNodeParams) unsigned char npbuf[sizeof(cudaGraphNodeParams)];
+    std::memset(npbuf, 0, sizeof(npbuf));
+    cudaGraphNodeParams& np = *reinterpret_cast<cudaGraphNodeParams*>(npbuf);
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = h;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, g, deps, nullptr, ndeps, &np));
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    CK(cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1, cudaStreamSetCaptureDependencies));
+    if (!ctx->body_stream) CK(cudaStreamCreateWithFlags(&ctx->body_stream, cudaStreamNonBlocking));
+    CK(cudaStreamBeginCaptureToGraph(ctx->body_stream, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal));
+    ctx->stream = ctx->body_stream;
+    const int64_t l0 = ctx->launches;
+    lbfs_status r = vcycle(ctx);
+    if (r == LBFS_OK) {
+        cudaStream_t b = ctx->body_stream;
+        cudaError_t e = launch_mg_correct(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], b);
+        if (e == cudaSuccess) e = launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], 0, b);
+        if (e == cudaSuccess)
+            e = launch_mg_finalize(p, ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, 0, K, nd, ticket, h, 1, b);
+        ctx->launches += 3;
+        if (e != cudaSuccess) r = fail(ctx, LBFS_ECUDA, std::string("cycle body: ") + cudaGetErrorString(e));
+    }
+    ctx->cycle_launches = ctx->launches - l0;
+    ctx->launches = l0;
+    ctx->stream = s;
+    cudaGraph_t out = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(ctx->body_stream, &out);
+    if (r != LBFS_OK) return r;
+    if (e2 != cudaSuccess) return fail(ctx, LBFS_ECUDA, std::string("cycle body capture: ") + cudaGetErrorString(e2));
+    return LBFS_OK;
+}
+
+// The warm potential solve as a graph of its own, launched by eager steps.
+lbfs_status build_pot_graph(lbfs_ctx* ctx) {
+    if (!ctx->cap_stream) CK(cudaStreamCreateWithFlags(&ctx->cap_stream, cudaStreamNonBlocking));
+    cudaStream_t user = ctx->stream;
+    const int64_t l0 = ctx->launches;
+    ctx->stream = ctx->cap_stream;
+    ctx->capturing = true;
+    cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
+    lbfs_status r = e == cudaSuccess ? capture_warm_potential(ctx) : LBFS_ECUDA;
+    cudaGraph_t g = nullptr;
+    cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
+    ctx->capturing = false;
+    ctx->stream = user;
+    ctx->launches = l0;
+    if (e != cudaSuccess) return fail(ctx, LBFS_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+    if (r != LBFS_OK) {
+        if (g) cudaGraphDestroy(g);
+        return r;
+    }
+    if (e2 != cudaSuccess) return fail(ctx, LBFS_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e2));
+    ctx->pot_graph = g;
+    CK(cudaGraphInstantiate(&ctx->pot_exec, g, 0));
+    return LBFS_OK;
+}
+
+// The potential of the current state.
+// After a state is set (pot_fresh), refinement cycles run until every case meets
+// mg_tol, checked on the host after each cycle (at most mg_max_cycles).
+// Every later step is the warm solve above (no host round trip): inline in a recorded
+// step graph, or its own graph launched by an eager step.  A case still above mg_tol
+// after mg_warm_cycles cycles is marked as failed (LBFS_ENOTCONVERGED at the end of
+// lbfs_step).  So the reported residual is always that of the potential the
+// thermo-fluid stages use.
 lbfs_status potential_solve(lbfs_ctx* ctx) {
     if (ctx->n_pot == 0) return LBFS_OK;
     const int p = ctx->prec;
     cudaStream_t s = ctx->stream;
-    const double no_fail = 1e300;
-    if (p != 0 && !ctx->pot_fresh) {
-        LK(launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], s));
-        LK(launch_mg_finalize(p, ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, ctx->mg_tol * 1e4, 1,
-                              ctx->d_flag, s));
-        lbfs_status r = vcycle(ctx);
-        if (r != LBFS_OK) return r;
-        LK(launch_mg_correct(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], s));
+    if (!ctx->pot_fresh) {
+        if (ctx->capturing) return capture_warm_potential(ctx);
+        if (!ctx->pot_exec) {
+            lbfs_status r = build_pot_graph(ctx);
+            if (r != LBFS_OK) return r;
+        }
+        CK(cudaGraphLaunch(ctx->pot_exec, s));
+        ctx->launches += 2;
         return LBFS_OK;
     }
     for (int it = 0;; ++it) {
-        LK(launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], s));
+        LK(launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], it == 0, s));
         CK(cudaMemsetAsync(ctx->d_flag, 0, sizeof(int), s));
-        LK(launch_mg_finalize(p, ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, no_fail, it == 0, ctx->d_flag, s));
+        LK(launch_mg_finalize(p, ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, it == 0, 1 << 30, ctx->d_flag,
+                              nullptr, 0, 0, s));
         CK(cudaMemcpyAsync(ctx->h_flag, ctx->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
         CK(cudaStreamSynchronize(s));
         if (*ctx->h_flag == 0) break;
@@ -418,10 +515,12 @@ lbfs_status record_graph(lbfs_ctx* ctx) {
     cudaStream_t user = ctx->stream;
     const int64_t l0 = ctx->launches;
     ctx->stream = ctx->cap_stream;
+    ctx->capturing = true;
     cudaError_t e = cudaStreamBeginCapture(ctx->cap_stream, cudaStreamCaptureModeThreadLocal);
     lbfs_status r = e == cudaSuccess ? one_step(ctx) : LBFS_ECUDA;
     cudaGraph_t g = nullptr;
     cudaError_t e2 = cudaStreamEndCapture(ctx->cap_stream, &g);
+    ctx->capturing = false;
     ctx->stream = user;
     ctx->graph_launches = ctx->launches - l0;
     ctx->launches = l0;
@@ -456,7 +555,8 @@ lbfs_status lbfs_create(const lbfs_config* cfg, lbfs_ctx** out) {
     if (!out) return LBFS_EINVAL;
     *out = nullptr;
     if (!cfg || cfg->max_cases < 1 || cfg->max_cases > 65536 || cfg->precision < 0 || cfg->precision > 1 ||
-        (cfg->dev_alloc == nullptr) != (cfg->dev_free == nullptr))
+        (cfg->dev_alloc == nullptr) != (cfg->dev_free == nullptr) || cfg->mg_warm_cycles < 0 ||
+        cfg->mg_warm_cycles > 64)
         return LBFS_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
@@ -469,6 +569,7 @@ lbfs_status lbfs_create(const lbfs_config* cfg, lbfs_ctx** out) {
     ctx->prec = cfg->precision;
     ctx->mg_tol = cfg->mg_tol > 0 ? cfg->mg_tol : (ctx->prec == 0 ? 1e-13 : 1e-6);
     ctx->mg_max_cycles = cfg->mg_max_cycles > 0 ? cfg->mg_max_cycles : 40;
+    ctx->mg_warm_cycles = cfg->mg_warm_cycles > 0 ? cfg->mg_warm_cycles : (ctx->prec == 0 ? 12 : 3);
     ctx->slots.resize(cfg->max_cases);
     ctx->tile = (cfg->tile >= 0 && cfg->tile < stage_tile_shapes()) ? cfg->tile : 0;
     if (cfg->cuda_stream) {
@@ -490,6 +591,7 @@ lbfs_status lbfs_create(const lbfs_config* cfg, lbfs_ctx** out) {
         return LBFS_ENOMEM;
     }
     cudaMemset(ctx->d_cases, 0, sizeof(DevCase) * cfg->max_cases);
+    cudaMemset(ctx->d_flag, 0, 256);   // [0] host-checked votes, [1] device votes, [2] ticket
     cudaMemset(ctx->d_stats, 0, sizeof(double) * kStatN * cfg->max_cases);
     if (cudaDeviceSynchronize() != cudaSuccess) {
         lbfs_destroy(ctx);
@@ -511,19 +613,33 @@ lbfs_status lbfs_set_case(lbfs_ctx* ctx, int32_t id, const lbfs_case_desc* desc)
     DevCase hd;
     std::memset(&hd, 0, sizeof(hd));
     hd.P = P;
+    // Each coarser level halves both cell counts, rounding up: level L's column I covers
+    // the fine columns [I 2^L, min((I + 1) 2^L, nx)), so only the last column (row) can
+    // be narrower; wlx (wly) is its width relative to the level's other cells.  A
+    // periodic axis of odd size cannot agglomerate across its wrap, so coarsening stops
+    // there.
     int nx = P.nx, ny = P.ny, nlev = 1;
     hd.lev[0].nx = nx;
     hd.lev[0].ny = ny;
-    while (nlev < kMaxLevels && nx % 2 == 0 && ny % 2 == 0 && nx * ny > kCoarsenCells && nx >= 4 && ny >= 4) {
-        nx /= 2;
-        ny /= 2;
-        hd.lev[nlev].nx = nx;
-        hd.lev[nlev].ny = ny;
+    hd.lev[0].wlx = hd.lev[0].wly = 1.0f;
+    hd.lev[0].ragged = 0;
+    while (nlev < kMaxLevels && nx * ny > kCoarsenCells && nx >= 4 && ny >= 4 && !(P.periodic_x && (nx & 1)) &&
+           !(P.periodic_y && (ny & 1))) {
+        nx = (nx + 1) / 2;
+        ny = (ny + 1) / 2;
+        const int sc = 1 << nlev;
+        MGLevel& lv = hd.lev[nlev];
+        lv.nx = nx;
+        lv.ny = ny;
+        lv.wlx = (float)(P.nx - (nx - 1) * sc) / (float)sc;
+        lv.wly = (float)(P.ny - (ny - 1) * sc) / (float)sc;
+        lv.ragged = (lv.wlx < 1.0f || lv.wly < 1.0f) ? 1 : 0;
         ++nlev;
     }
     if (P.solve_potential && nx * ny > kCoarsestMax)
         return fail(ctx, LBFS_EINVAL,
-                    "grid sizes do not coarsen to <= 4096 cells by halving (use sizes with more factors of 2)");
+                    "the potential's coarsest level would exceed 4096 cells (a periodic axis whose size "
+                    "halves to an odd number early, or an extreme aspect ratio)");
     hd.nlev = nlev;
     fill_phys<float>(P, hd.qf);
     fill_phys<double>(P, hd.qd);
@@ -709,12 +825,14 @@ lbfs_status lbfs_step(lbfs_ctx* ctx, int32_t nsteps, lbfs_case_stats* out) {
     ctx->launches = 0;
     ctx->pot_fail = false;
     for (size_t c = 0; c < ctx->slots.size(); ++c)
-        if (ctx->slots[c].defined)
+        if (ctx->slots[c].defined) {
             CK(cudaMemsetAsync(ctx->d_stats + c * kStatN + ST_POT_FAIL, 0, sizeof(double), ctx->stream));
+            // ST_POT_RESID_MAX, ST_POT_CYCLES_SUM, ST_STEPS_CALL: per-call accumulators
+            CK(cudaMemsetAsync(ctx->d_stats + c * kStatN + ST_POT_RESID_MAX, 0, 3 * sizeof(double), ctx->stream));
+        }
     for (int n = 0; n < nsteps && ctx->n_active > 0; ++n) {
-        // a warm mixed-precision step has no host round trip and can be replayed
-        const bool graphable = ctx->cfg.use_graph && !ctx->timing && (ctx->prec != 0 || ctx->n_pot == 0) &&
-                               !(ctx->n_pot > 0 && ctx->pot_fresh);
+        // a step after the first potential solve has no host round trip and can be replayed
+        const bool graphable = ctx->cfg.use_graph && !ctx->timing && !(ctx->n_pot > 0 && ctx->pot_fresh);
         if (graphable) {
             if (!ctx->gexec) {
                 lbfs_status r = record_graph(ctx);
@@ -731,6 +849,13 @@ lbfs_status lbfs_step(lbfs_ctx* ctx, int32_t nsteps, lbfs_case_stats* out) {
     CK(cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, nb, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     harvest(ctx);
+    if (ctx->n_pot > 0 && ctx->cycle_launches > 0) {
+        // refinement cycles run by device-decided loops: at least the most any case ran
+        double cyc = 0.0;
+        for (size_t c = 0; c < ctx->slots.size(); ++c)
+            if (ctx->slots[c].defined) cyc = std::fmax(cyc, ctx->h_stats[c * kStatN + ST_POT_CYCLES_SUM]);
+        ctx->launches += (int64_t)cyc * ctx->cycle_launches;
+    }
     bool bad = false;
     for (size_t c = 0; c < ctx->slots.size(); ++c) {
         const double* st = ctx->h_stats + c * kStatN;
@@ -750,11 +875,14 @@ lbfs_status lbfs_step(lbfs_ctx* ctx, int32_t nsteps, lbfs_case_stats* out) {
             o.pot_resid = st[ST_POT_RESID];
             o.pot_cycles = (int32_t)st[ST_POT_CYCLES];
             o.nonfinite = st[ST_NONFINITE] > 0 ? 1 : 0;
+            o.pot_resid_max = st[ST_POT_RESID_MAX];
+            o.pot_cycles_mean = st[ST_STEPS_CALL] > 0 ? st[ST_POT_CYCLES_SUM] / st[ST_STEPS_CALL] : 0.0;
         }
     }
     if (bad) return fail(ctx, LBFS_EDIVERGED, "a non-finite value appeared in a case's state");
     if (ctx->pot_fail)
-        return fail(ctx, LBFS_ENOTCONVERGED, "the potential solve missed its tolerance in mg_max_cycles");
+        return fail(ctx, LBFS_ENOTCONVERGED,
+                    "the potential solve missed mg_tol within mg_max_cycles (first solve) or mg_warm_cycles");
     return LBFS_OK;
 }
 
@@ -834,6 +962,7 @@ void lbfs_destroy(lbfs_ctx* ctx) {
     harvest(ctx);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     if (ctx->cap_stream) cudaStreamDestroy(ctx->cap_stream);
+    if (ctx->body_stream) cudaStreamDestroy(ctx->body_stream);
     for (Slot& s : ctx->slots) free_slot(ctx, s);
     for (auto* p : ctx->d_mg_tiles) dfree(ctx, p);
     for (auto* p : ctx->d_ft_tiles) dfree(ctx, p);

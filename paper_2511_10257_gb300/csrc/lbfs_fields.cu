@@ -345,6 +345,11 @@ __global__ void k_step_finalize(const DevCase* __restrict__ cases, const int* __
         st[ST_T_FREEZE] = (st[ST_T] - dt) + dt * (0.99 - q0) / (QL - q0);
     }
     st[ST_QL_PREV] = QL;
+    if (dc->P.solve_potential) {
+        st[ST_POT_RESID_MAX] = fmax(st[ST_POT_RESID_MAX], st[ST_POT_RESID]);
+        st[ST_POT_CYCLES_SUM] += st[ST_POT_CYCLES];
+    }
+    st[ST_STEPS_CALL] += 1.0;
 }
 
 }  // namespace

@@ -10,13 +10,14 @@ namespace lbfs {
 constexpr int kMaxLevels = 16;
 constexpr int kRedN = 6;        // per-tile partial sums of the step-end reduction
 constexpr int kFinChunks = 32;  // blocks per case that reduce the tile partials
-constexpr int kStatN = 16;      // per-case device statistics slots
+constexpr int kStatN = 20;      // per-case device statistics slots
 
-// statistics slots (FP64, per case)
+// statistics slots (FP64, per case).  ST_POT_RESID_MAX, ST_POT_CYCLES_SUM and
+// ST_STEPS_CALL accumulate over the steps of one lbfs_step call.
 enum StatSlot {
     ST_SUM_C = 0, ST_SUM_HE, ST_SUM_FL_DROP, ST_N_DROP, ST_Q_L, ST_T, ST_T_FREEZE,
     ST_POT_RESID, ST_POT_CYCLES, ST_NONFINITE, ST_QL_PREV, ST_POT_DONE, ST_B2, ST_STEP,
-    ST_POT_FAIL, ST_SPARE
+    ST_POT_FAIL, ST_POT_RESID_MAX, ST_POT_CYCLES_SUM, ST_STEPS_CALL, ST_SPARE0, ST_SPARE1
 };
 
 // Physical and numerical parameters of one case, resolved on the host in FP64.
@@ -50,6 +51,11 @@ struct PhysT {
 
 struct MGLevel {
     int nx, ny, pitch;
+    // Coarse levels halve the cell count with the size rounded up, so the last column
+    // (row) of a level may cover fewer fine cells than the others: wlx (wly) is its
+    // width (height) relative to the level's other cells, 1 when the level is regular.
+    float wlx, wly;
+    int ragged;  // wlx < 1 or wly < 1
     void* mu;   // cell coefficient mu_m (M precision)
     void* e;    // correction
     void* r;    // right-hand side / residual
@@ -82,6 +88,8 @@ struct DevCase {
     double* stats;    // kStatN FP64 slots
 };
 
+// One block's work: the tile at (x0, y0) of a case; slot numbers the case's
+// partial-sum entries.
 struct TileRef {
     int case_id, x0, y0, slot;
 };

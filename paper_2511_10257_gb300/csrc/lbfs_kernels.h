@@ -17,17 +17,23 @@ int stage_tile_h(int prec, int tile);
 cudaError_t launch_stage(int prec, int tile, int half, const DevCase* cases, const TileRef* tiles,
                          int ntiles, int stage, cudaStream_t st);
 
-// potential multigrid (lbfs_potential.cu).  MG tiles are 32 x 8 cells of one level.
-constexpr int kMgTX = 32, kMgTY = 8;
-cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* tiles, int n,
+// potential multigrid (lbfs_potential.cu).  The fine-level cell kernels (residual,
+// correction) take 32 x 32 tiles.  first: the step's first residual (every case);
+// later ones skip converged cases.
+constexpr int kMgTX = 32, kMgTY = 32;
+cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* tiles, int n, int first,
                                  cudaStream_t st);
-// tol: the convergence test; a residual above fail_tol marks the case's solve failed
+// tol: the convergence test.  first: the step's first check.  A case still above tol
+// gets another cycle (one more vote in not_done) unless it has had kmax, when it is
+// marked as failed.  set_cond: the call runs inside a conditional graph node; the
+// last case to decide (ticket) sets cond to 1 while a case needs another cycle.
 // `iters` explicit pseudo-time steps of the paper's magnetic LBFS (Eqs. 12-18) on one
 // case, FP64 arithmetic; tmp holds nx*ny doubles.  2 launches per step.
 cudaError_t launch_pseudo_time(int prec, const DevCase* dcase, int nx, int ny, int iters, double dtau,
                                double* tmp, cudaStream_t st);
-cudaError_t launch_mg_finalize(int prec, const DevCase* cases, const int* case_ids, int ncases, double tol,
-                               double fail_tol, int first, int* not_done, cudaStream_t st);
+cudaError_t launch_mg_finalize(int prec, const DevCase* cases, const int* case_ids, int ncases, double tol, int first,
+                               int kmax, int* not_done, unsigned* ticket, cudaGraphConditionalHandle cond,
+                               int set_cond, cudaStream_t st);
 cudaError_t launch_mg_coarsest(int prec, const DevCase* cases, const int* case_ids, int ncases,
                                int max_cells, cudaStream_t st);
 cudaError_t launch_mg_correct(int prec, const DevCase* cases, const TileRef* tiles, int n,

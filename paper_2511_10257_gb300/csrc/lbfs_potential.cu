@@ -8,16 +8,23 @@
 // Operator (per level, homogeneous walls for the correction):
 //   (A x)_c = sum_nb mu_f (x_c - x_nb) + sum_Dirichlet-walls 2 mu_c x_c,
 //   mu_f = (mu_c + mu_nb)/2, b_c = sum_Dirichlet-walls 2 mu_c phi_wall.
-// Coarse levels: 2 x 2 agglomeration, mu averaged, residual summed (the 2-D
-// finite-volume operator is scale free), bilinear cell-centred prolongation,
-// red-black Gauss-Seidel smoothing, conjugate gradients on the coarsest level.
+// Coarse levels: 2 x 2 agglomeration with the cell count rounded up, mu averaged over
+// the children, residual summed (the 2-D finite-volume operator is scale free),
+// bilinear cell-centred prolongation, red-black Gauss-Seidel smoothing, conjugate
+// gradients on the coarsest level.  On a level of odd size the last column (row)
+// agglomerates a single child and is narrower than the others; its face coefficients
+// carry the true face length over centre distance, and the prolongation interpolates
+// between the true centres, so every grid size keeps the contraction of the even
+// ones.
 #include "lbfs_kernels.h"
 
 namespace lbfs {
 
 namespace {
 
-constexpr int kNT = kMgTX * kMgTY;  // 256 threads, one per cell of a 32 x 8 tile
+constexpr int kNT = 256;                 // threads of the fine-level cell kernels
+constexpr int kRowsPT = kMgTY / (kNT / kMgTX);  // rows of a 32 x 32 tile per thread (4)
+static_assert(kRowsPT * (kNT / kMgTX) == kMgTY, "a fine-level tile splits evenly over the threads");
 
 __device__ __forceinline__ bool pot_done(const DevCase* dc) {
     return dc->stats[ST_POT_DONE] >= 1.0;
@@ -40,6 +47,53 @@ __device__ __forceinline__ int neighbour(const CaseParams& P, int nx, int ny, in
     return 1;
 }
 
+// ---- geometry of a level whose last column or row may be narrower -------------
+template <class M>
+__device__ __forceinline__ M cell_wx(const MGLevel& lv, int i) {
+    return i == lv.nx - 1 ? M(lv.wlx) : M(1);
+}
+template <class M>
+__device__ __forceinline__ M cell_wy(const MGLevel& lv, int j) {
+    return j == lv.ny - 1 ? M(lv.wly) : M(1);
+}
+// Face length over centre distance, in the level's cell units, for the face of cell
+// (i, j) on side w (0 -x, 1 +x, 2 -y, 3 +y): to the neighbour cell, or to the wall half
+// the cell's width away.  1 and 2 for regular cells.
+template <class M>
+__device__ __forceinline__ M face_factor(const MGLevel& lv, int i, int j, int w, bool wall) {
+    const M wx = cell_wx<M>(lv, i), wy = cell_wy<M>(lv, j);
+    if (w < 2) {
+        const M d = wall ? M(0.5) * wx : M(0.5) * (wx + cell_wx<M>(lv, w == 0 ? i - 1 : i + 1));
+        return wy / d;
+    }
+    const M d = wall ? M(0.5) * wy : M(0.5) * (wy + cell_wy<M>(lv, w == 2 ? j - 1 : j + 1));
+    return wx / d;
+}
+
+// Prolongation along one axis: the fine cell i of a level with nf cells (last width
+// wlf) takes 1 - w of its parent I = floor(i/2) on the coarse level (nc cells, last
+// width wlc) and w of the coarse neighbour I + d, d in {-1, 0, 1}, by linear
+// interpolation between the true centres (in fine-cell units).  Across a wall the
+// neighbour is the parent's mirror image about the wall.  Regular cells give w = 1/4.
+template <class M>
+__device__ __forceinline__ void prolong_axis(int i, int nf, float wlf, int nc, float wlc, int& d, M& w) {
+    const M xf = M(i) + (i == nf - 1 ? M(0.5f * wlf) : M(0.5));
+    const int I = (i >= 0 ? i : i - 1) / 2;
+    const M xp = M(2 * I) + (I == nc - 1 ? M(wlc) : M(1));
+    if (xf == xp) {
+        d = 0;
+        w = M(0);
+        return;
+    }
+    d = xf > xp ? 1 : -1;
+    const int N = I + d;
+    M xn;
+    if (N < 0) xn = -xp;
+    else if (N >= nc) xn = M(4 * (nc - 1)) + M(4) * M(wlc) - xp;
+    else xn = M(2 * N) + (N == nc - 1 ? M(wlc) : M(1));
+    w = (xf - xp) / (xn - xp);
+}
+
 template <class T>
 __device__ __forceinline__ T block_sum(T v, T* sh) {
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -53,10 +107,10 @@ __device__ __forceinline__ T block_sum(T v, T* sh) {
     return tot;
 }
 
-// (A x)_c with the level's coefficient, homogeneous Dirichlet walls
+// (A x)_c with the level's coefficient and geometry, homogeneous Dirichlet walls
 template <class M>
-__device__ __forceinline__ M apply_A(const CaseParams& P, const M* mu, const M* x, int nx, int ny,
-                                     int pitch, int i, int j) {
+__device__ __forceinline__ M apply_A(const CaseParams& P, const MGLevel& lv, const M* mu, const M* x, int nx,
+                                     int ny, int pitch, int i, int j) {
     const M mc = mu[(size_t)j * pitch + i];
     const M xc = x[(size_t)j * pitch + i];
     M acc = 0;
@@ -65,9 +119,10 @@ __device__ __forceinline__ M apply_A(const CaseParams& P, const M* mu, const M* 
         int ii, jj;
         if (neighbour(P, nx, ny, i, j, w, ii, jj)) {
             const size_t kn = (size_t)jj * pitch + ii;
-            acc += M(0.5) * (mc + mu[kn]) * (xc - x[kn]);
+            if (lv.ragged) acc += face_factor<M>(lv, i, j, w, false) * M(0.5) * (mc + mu[kn]) * (xc - x[kn]);
+            else acc += M(0.5) * (mc + mu[kn]) * (xc - x[kn]);
         } else if (P.mag_dir[w]) {
-            acc += M(2) * mc * xc;
+            acc += (lv.ragged ? face_factor<M>(lv, i, j, w, true) : M(2)) * mc * xc;
         }
     }
     return acc;
@@ -165,34 +220,43 @@ __device__ __forceinline__ float residual_cell_f(const DevCase* dc, const CasePa
     return -__fadd_rn(ah, al);
 }
 
+// One block per 32 x 32 tile of the fine level, each thread four rows of a column
+// (rows interleaved so that a warp covers one row); the tile's partial norms are
+// reduced once.  first: the step's first residual, which every case computes; later
+// residuals skip the cases whose solve has converged.
 template <class M>
 __global__ void __launch_bounds__(kNT) k_residual64(const DevCase* __restrict__ cases,
-                                                    const TileRef* __restrict__ tiles) {
+                                                    const TileRef* __restrict__ tiles, int first) {
     using Slot = typename DSum<M>::Slot;
     __shared__ Slot sh[32];
     const TileRef tr = tiles[blockIdx.x];
     const DevCase* dc = cases + tr.case_id;
+    if (!first && pot_done(dc)) return;
     const CaseParams& P = dc->P;
     const MGLevel lv = dc->lev[0];
-    const int i = tr.x0 + threadIdx.x % kMgTX, j = tr.y0 + threadIdx.x / kMgTX;
     DSum<M> r2 = DSum<M>::zero(), b2 = DSum<M>::zero();
-    if (i < lv.nx && j < lv.ny) {
-        const size_t k = (size_t)j * lv.pitch + i;
-        double b;
-        if constexpr (sizeof(M) == 8) {
-            const double r = residual_cell<double>(dc, P, lv, i, j, b);
-            static_cast<double*>(lv.r)[k] = r;
-            r2.add(r * r);
-            b2.add(b * b);
-        } else {
-            bool has_b;
-            const float r = residual_cell_f(dc, P, lv, i, j, b, has_b);
-            static_cast<float*>(lv.r)[k] = r;
-            r2.add(r * r);
-            if (has_b) {
-                float2 bb;
-                pair_from(b * b, bb.x, bb.y);
-                b2.add(bb);
+    const int i = tr.x0 + threadIdx.x % kMgTX;
+#pragma unroll
+    for (int q = 0; q < kRowsPT; ++q) {
+        const int j = tr.y0 + threadIdx.x / kMgTX + q * (kNT / kMgTX);
+        if (i < lv.nx && j < lv.ny) {
+            const size_t k = (size_t)j * lv.pitch + i;
+            double b;
+            if constexpr (sizeof(M) == 8) {
+                const double r = residual_cell<double>(dc, P, lv, i, j, b);
+                static_cast<double*>(lv.r)[k] = r;
+                r2.add(r * r);
+                b2.add(b * b);
+            } else {
+                bool has_b;
+                const float r = residual_cell_f(dc, P, lv, i, j, b, has_b);
+                static_cast<float*>(lv.r)[k] = r;
+                r2.add(r * r);
+                if (has_b) {
+                    float2 bb;
+                    pair_from(b * b, bb.x, bb.y);
+                    b2.add(bb);
+                }
             }
         }
     }
@@ -205,16 +269,39 @@ __global__ void __launch_bounds__(kNT) k_residual64(const DevCase* __restrict__ 
     }
 }
 
+// The one call of cudaGraphSetConditional of a check: every case adds one to the ticket
+// after it has added its vote to not_done; the last one sets the loop condition (run
+// another cycle while a case still needs one) and clears both counters.
+__device__ __forceinline__ void decide_next_cycle(int* not_done, unsigned* ticket, int ncases,
+                                                  cudaGraphConditionalHandle cond) {
+    __threadfence();
+    if (atomicAdd(ticket, 1u) == (unsigned)(ncases - 1)) {
+        __threadfence();
+        const int nd = atomicExch(not_done, 0);
+        *ticket = 0u;
+        cudaGraphSetConditional(cond, nd > 0 ? 1u : 0u);
+    }
+}
+
 // relative residual, convergence flag, cycle count: kFinChunks blocks per case sum
 // fixed contiguous ranges of the tile partials; the last block to finish (a ticket,
-// no waiting) sums the chunk sums in chunk order and decides
+// no waiting) sums the chunk sums in chunk order and decides.  first: the step's
+// first check (resets the cycle count); later checks skip converged cases.  A case
+// that has not converged gets another cycle unless it has had kmax, in which case it
+// is marked as failed and left alone.  set_cond: inside a conditional graph, the last
+// case to decide sets whether the loop runs another cycle.
 template <class M>
-__global__ void k_mg_finalize(const DevCase* __restrict__ cases, const int* __restrict__ ids,
-                              double tol, double fail_tol, int first, int* not_done) {
+__global__ void k_mg_finalize(const DevCase* __restrict__ cases, const int* __restrict__ ids, double tol,
+                              int first, int kmax, int* not_done, unsigned* ticket, int ncases,
+                              cudaGraphConditionalHandle cond, int set_cond) {
     using Slot = typename DSum<M>::Slot;
     __shared__ Slot sh[32];
     __shared__ bool last;
     const DevCase* dc = cases + ids[blockIdx.y];
+    if (!first && pot_done(dc)) {
+        if (set_cond && blockIdx.x == 0 && threadIdx.x == 0) decide_next_cycle(not_done, ticket, ncases, cond);
+        return;
+    }
     const int T = dc->mg_tiles, c = blockIdx.x;
     const int t0 = (int)((long long)T * c / kFinChunks), t1 = (int)((long long)T * (c + 1) / kFinChunks);
     const Slot* red = static_cast<const Slot*>(dc->mg_red);
@@ -246,13 +333,18 @@ __global__ void k_mg_finalize(const DevCase* __restrict__ cases, const int* __re
     double* st = dc->stats;
     st[ST_POT_RESID] = rel;
     const bool done = rel <= tol;
-    st[ST_POT_DONE] = done ? 1.0 : 0.0;
-    if (rel > fail_tol) st[ST_POT_FAIL] = 1.0;
     if (first) st[ST_POT_CYCLES] = 0.0;
-    if (!done) {
+    if (done) {
+        st[ST_POT_DONE] = 1.0;
+    } else if (st[ST_POT_CYCLES] >= (double)kmax) {
+        st[ST_POT_FAIL] = 1.0;
+        st[ST_POT_DONE] = 1.0;   // no further kernel of this step touches the case
+    } else {
+        st[ST_POT_DONE] = 0.0;
         st[ST_POT_CYCLES] += 1.0;
         atomicAdd(not_done, 1);
     }
+    if (set_cond) decide_next_cycle(not_done, ticket, ncases, cond);
 }
 
 // coarse value at (I, J), possibly one cell outside: periodic wrap, Dirichlet wall
@@ -321,9 +413,70 @@ __device__ __forceinline__ int region_source(const CaseParams& P, int nx, int ny
 // Threads take only the cells of colour c (every other cell of a row), and a
 // neighbour is a cell exactly when its region entry lies inside the domain (in[]),
 // which is how the level's walls and periodic wraps were resolved at load time.
+// (A x) at region cell k of a tile at (x0, y0), split into its diagonal and the
+// neighbour sum: A x = diag x_k - off.  Regular levels take the plain five-point
+// coefficients; a ragged level the geometric factors of its narrower last cells.
 template <class M, int H>
-__device__ __forceinline__ void region_half_sweep(const CaseParams& P, int x0, int y0, const M* mu, const M* r,
-                                                  M* e, const unsigned char* in, int c, int h) {
+__device__ __forceinline__ void region_stencil(const CaseParams& P, const MGLevel& lv, int x0, int y0,
+                                               const M* mu, const M* x, const unsigned char* in, int k,
+                                               M& diag, M& off) {
+    using G = FRegion<H>;
+    const M mc = mu[k];
+    diag = 0;
+    off = 0;
+    if (!lv.ragged) {
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int kn = k + (w == 0 ? -1 : w == 1 ? 1 : w == 2 ? -G::W : G::W);
+            if (in[kn]) {
+                const M mf = M(0.5) * (mc + mu[kn]);
+                diag += mf;
+                off += mf * x[kn];
+            } else if (P.mag_dir[w]) {
+                diag += M(2) * mc;
+            }
+        }
+        return;
+    }
+    const int gx = x0 - H + k % G::W, gy = y0 - H + k / G::W;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const int kn = k + (w == 0 ? -1 : w == 1 ? 1 : w == 2 ? -G::W : G::W);
+        if (in[kn]) {
+            const M mf = face_factor<M>(lv, gx, gy, w, false) * M(0.5) * (mc + mu[kn]);
+            diag += mf;
+            off += mf * x[kn];
+        } else if (P.mag_dir[w]) {
+            diag += face_factor<M>(lv, gx, gy, w, true) * mc;
+        }
+    }
+}
+
+// (A x) at region cell k in difference form, sum_f g mu_f (x_k - x_nb) + walls
+template <class M, int H>
+__device__ __forceinline__ M region_apply(const CaseParams& P, const MGLevel& lv, int x0, int y0, const M* mu,
+                                          const M* x, const unsigned char* in, int k) {
+    using G = FRegion<H>;
+    const M mc = mu[k], xc = x[k];
+    M ax = 0;
+    const int gx = x0 - H + k % G::W, gy = y0 - H + k / G::W;
+#pragma unroll
+    for (int w = 0; w < 4; ++w) {
+        const int kn = k + (w == 0 ? -1 : w == 1 ? 1 : w == 2 ? -G::W : G::W);
+        if (in[kn]) {
+            if (lv.ragged) ax += face_factor<M>(lv, gx, gy, w, false) * M(0.5) * (mc + mu[kn]) * (xc - x[kn]);
+            else ax += M(0.5) * (mc + mu[kn]) * (xc - x[kn]);
+        } else if (P.mag_dir[w]) {
+            ax += (lv.ragged ? face_factor<M>(lv, gx, gy, w, true) : M(2)) * mc * xc;
+        }
+    }
+    return ax;
+}
+
+template <class M, int H>
+__device__ __forceinline__ void region_half_sweep(const CaseParams& P, const MGLevel& lv, int x0, int y0,
+                                                  const M* mu, const M* r, M* e, const unsigned char* in, int c,
+                                                  int h) {
     using G = FRegion<H>;
     const int VW = G::W - 2 * h, VH = G::Hh - 2 * h, HW = (VW + 1) / 2;
     const int base = (x0 - H) + (y0 - H);
@@ -333,19 +486,8 @@ __device__ __forceinline__ void region_half_sweep(const CaseParams& P, int x0, i
         if (lx >= G::W - h) continue;
         const int k = ly * G::W + lx;
         if (!in[k]) continue;
-        const M mc = mu[k];
-        M diag = 0, off = 0;
-#pragma unroll
-        for (int w = 0; w < 4; ++w) {
-            const int kn = k + (w == 0 ? -1 : w == 1 ? 1 : w == 2 ? -G::W : G::W);
-            if (in[kn]) {
-                const M mf = M(0.5) * (mc + mu[kn]);
-                diag += mf;
-                off += mf * e[kn];
-            } else if (P.mag_dir[w]) {
-                diag += M(2) * mc;
-            }
-        }
+        M diag, off;
+        region_stencil<M, H>(P, lv, x0, y0, mu, e, in, k, diag, off);
         e[k] = fdiv(r[k] + off, diag);
     }
 }
@@ -382,7 +524,7 @@ __global__ void __launch_bounds__(256) k_vdown(const DevCase* __restrict__ cases
     region_load<M, kHD>(P, lv, tr.x0, tr.y0, smu, sr, se, in, false);
     __syncthreads();
     for (int h = 1; h <= 2 * kFNu; ++h) {
-        region_half_sweep<M, kHD>(P, tr.x0, tr.y0, smu, sr, se, in, (h - 1) & 1, h);
+        region_half_sweep<M, kHD>(P, lv, tr.x0, tr.y0, smu, sr, se, in, (h - 1) & 1, h);
         __syncthreads();
     }
     // pre-smoothed correction of the tile
@@ -392,7 +534,8 @@ __global__ void __launch_bounds__(256) k_vdown(const DevCase* __restrict__ cases
         if (gx < lv.nx && gy < lv.ny)
             e[(size_t)gy * lv.pitch + gx] = se[(t / kFTX + kHD) * G::W + t % kFTX + kHD];
     }
-    // restricted residual r - A e over the 2 x 2 children of each coarse cell, and
+    // restricted residual r - A e over the children of each coarse cell (four, or
+    // fewer where the coarse cell is the narrower last one of its row or column), and
     // the coarse coefficient as the mean of the children's
     M* rc = static_cast<M*>(cv.r);
     M* muc = static_cast<M*>(cv.mu);
@@ -403,25 +546,23 @@ __global__ void __launch_bounds__(256) k_vdown(const DevCase* __restrict__ cases
         M acc = 0;
         {
             const int k0 = (kHD + 2 * cj) * G::W + kHD + 2 * ci;
-            muc[(size_t)J * cv.pitch + I] =
-                M(0.25) * ((smu[k0] + smu[k0 + 1]) + (smu[k0 + G::W] + smu[k0 + G::W + 1]));
+            if (in[k0 + 1] && in[k0 + G::W]) {
+                muc[(size_t)J * cv.pitch + I] =
+                    M(0.25) * ((smu[k0] + smu[k0 + 1]) + (smu[k0 + G::W] + smu[k0 + G::W + 1]));
+            } else {
+                M m = smu[k0];
+                int n = 1;
+                if (in[k0 + 1]) { m += smu[k0 + 1]; ++n; }
+                if (in[k0 + G::W]) { m += smu[k0 + G::W]; ++n; }
+                muc[(size_t)J * cv.pitch + I] = m / M(n);
+            }
         }
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
             const int lx = kHD + 2 * ci + (q & 1), ly = kHD + 2 * cj + (q >> 1);
             const int k = ly * G::W + lx;
-            const M mc = smu[k], xc = se[k];
-            M ax = 0;
-#pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                const int kn = k + (w == 0 ? -1 : w == 1 ? 1 : w == 2 ? -G::W : G::W);
-                if (in[kn]) {
-                    ax += M(0.5) * (mc + smu[kn]) * (xc - se[kn]);
-                } else if (P.mag_dir[w]) {
-                    ax += M(2) * mc * xc;
-                }
-            }
-            acc += sr[k] - ax;
+            if (!in[k]) continue;
+            acc += sr[k] - region_apply<M, kHD>(P, lv, tr.x0, tr.y0, smu, se, in, k);
         }
         rc[(size_t)J * cv.pitch + I] = acc;
     }
@@ -461,15 +602,25 @@ __global__ void __launch_bounds__(256) k_vup(const DevCase* __restrict__ cases,
         const int gx = tr.x0 - kHU + k % G::W, gy = tr.y0 - kHU + k / G::W;
         // parent of the region cell in unwrapped level coordinates
         const int I = (gx >= 0 ? gx : gx - 1) / 2, J = (gy >= 0 ? gy : gy - 1) / 2;
-        const int di = (gx & 1) ? 1 : -1, dj = (gy & 1) ? 1 : -1;
         const int a = (J - cy0) * CW + (I - cx0);
-        const M v = M(9.0 / 16.0) * sc[a] + M(3.0 / 16.0) * sc[a + di] + M(3.0 / 16.0) * sc[a + dj * CW] +
-                    M(1.0 / 16.0) * sc[a + di + dj * CW];
+        M v;
+        if (!lv.ragged && !cv.ragged) {
+            const int di = (gx & 1) ? 1 : -1, dj = (gy & 1) ? 1 : -1;
+            v = M(9.0 / 16.0) * sc[a] + M(3.0 / 16.0) * sc[a + di] + M(3.0 / 16.0) * sc[a + dj * CW] +
+                M(1.0 / 16.0) * sc[a + di + dj * CW];
+        } else {
+            int di, dj;
+            M wx, wy;
+            prolong_axis<M>(gx, lv.nx, lv.wlx, cv.nx, cv.wlx, di, wx);
+            prolong_axis<M>(gy, lv.ny, lv.wly, cv.ny, cv.wly, dj, wy);
+            v = ((M(1) - wx) * (M(1) - wy)) * sc[a] + (wx * (M(1) - wy)) * sc[a + di] +
+                ((M(1) - wx) * wy) * sc[a + dj * CW] + (wx * wy) * sc[a + di + dj * CW];
+        }
         se[k] += v;
     }
     __syncthreads();
     for (int h = 1; h <= 2 * kFNu; ++h) {
-        region_half_sweep<M, kHU>(P, tr.x0, tr.y0, smu, sr, se, in, (h - 1) & 1, h);
+        region_half_sweep<M, kHU>(P, lv, tr.x0, tr.y0, smu, sr, se, in, (h - 1) & 1, h);
         __syncthreads();
     }
     M* e = static_cast<M*>(lv.e);
@@ -516,7 +667,7 @@ __global__ void __launch_bounds__(256) k_coarsest(const DevCase* __restrict__ ca
     for (int it = 0; it < maxit && rr > tol2 * rr0 && rr > M(0); ++it) {
         M pAp = 0;
         for (int k = threadIdx.x; k < n; k += blockDim.x) {
-            const M a = apply_A<M>(P, mu, p, nx, ny, nx, k % nx, k / nx);
+            const M a = apply_A<M>(P, lv, mu, p, nx, ny, nx, k % nx, k / nx);
             Ap[k] = a;
             pAp += p[k] * a;
         }
@@ -547,19 +698,24 @@ __global__ void __launch_bounds__(kNT) k_correct(const DevCase* __restrict__ cas
     const DevCase* dc = cases + tr.case_id;
     if (pot_done(dc)) return;
     const MGLevel lv = dc->lev[0];
-    const int i = tr.x0 + threadIdx.x % kMgTX, j = tr.y0 + threadIdx.x / kMgTX;
-    if (i >= lv.nx || j >= lv.ny) return;
-    const size_t k = (size_t)j * lv.pitch + i;
-    if (sizeof(M) == 8) {
-        const double v = dc->phi64[k] + (double)static_cast<const M*>(lv.e)[k];
-        dc->phi64[k] = v;
-    } else {
-        // (phi, phi_lo) += e as a renormalised FP32 pair
-        float* hi = static_cast<float*>(dc->phi);
-        float h = hi[k], l = dc->phi_lo[k];
-        pair_add(h, l, (float)static_cast<const M*>(lv.e)[k], 0.f);
-        hi[k] = h;
-        dc->phi_lo[k] = l;
+    const int i = tr.x0 + threadIdx.x % kMgTX;
+    if (i >= lv.nx) return;
+#pragma unroll
+    for (int q = 0; q < kRowsPT; ++q) {
+        const int j = tr.y0 + threadIdx.x / kMgTX + q * (kNT / kMgTX);
+        if (j >= lv.ny) break;
+        const size_t k = (size_t)j * lv.pitch + i;
+        if (sizeof(M) == 8) {
+            const double v = dc->phi64[k] + (double)static_cast<const M*>(lv.e)[k];
+            dc->phi64[k] = v;
+        } else {
+            // (phi, phi_lo) += e as a renormalised FP32 pair
+            float* hi = static_cast<float*>(dc->phi);
+            float h = hi[k], l = dc->phi_lo[k];
+            pair_add(h, l, (float)static_cast<const M*>(lv.e)[k], 0.f);
+            hi[k] = h;
+            dc->phi_lo[k] = l;
+        }
     }
 }
 
@@ -674,20 +830,25 @@ cudaError_t launch_pseudo_time(int prec, const DevCase* d, int nx, int ny, int i
     return cudaGetLastError();
 }
 
-cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* tiles, int n,
+cudaError_t launch_mg_residual64(int prec, const DevCase* cases, const TileRef* tiles, int n, int first,
                                  cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    if (prec == 0) k_residual64<double><<<n, kNT, 0, st>>>(cases, tiles);
-    else k_residual64<float><<<n, kNT, 0, st>>>(cases, tiles);
+    if (prec == 0) k_residual64<double><<<n, kNT, 0, st>>>(cases, tiles, first);
+    else k_residual64<float><<<n, kNT, 0, st>>>(cases, tiles, first);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mg_finalize(int prec, const DevCase* cases, const int* ids, int ncases, double tol,
-                               double fail_tol, int first, int* not_done, cudaStream_t st) {
+cudaError_t launch_mg_finalize(int prec, const DevCase* cases, const int* ids, int ncases, double tol, int first,
+                               int kmax, int* not_done, unsigned* ticket, cudaGraphConditionalHandle cond,
+                               int set_cond, cudaStream_t st) {
     if (ncases <= 0) return cudaSuccess;
     const dim3 grid(kFinChunks, ncases);
-    if (prec == 0) k_mg_finalize<double><<<grid, 256, 0, st>>>(cases, ids, tol, fail_tol, first, not_done);
-    else k_mg_finalize<float><<<grid, 256, 0, st>>>(cases, ids, tol, fail_tol, first, not_done);
+    if (prec == 0)
+        k_mg_finalize<double><<<grid, 256, 0, st>>>(cases, ids, tol, first, kmax, not_done, ticket, ncases, cond,
+                                                    set_cond);
+    else
+        k_mg_finalize<float><<<grid, 256, 0, st>>>(cases, ids, tol, first, kmax, not_done, ticket, ncases, cond,
+                                                   set_cond);
     return cudaGetLastError();
 }
 

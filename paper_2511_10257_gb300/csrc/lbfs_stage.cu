@@ -84,66 +84,89 @@ __device__ __forceinline__ void side_sums(const R c[7], const R h[7], R r0, R r1
     }
 }
 
+// The cells one face reads, as offsets into a field's shared array: A (lower/left)
+// and B (upper/right), the cells beyond them along the normal (Am = A - n, Bp = B + n)
+// and their neighbours along the tangent (Atp/Atm = A +- t, Btp/Btm = B +- t).
+struct FaceCells {
+    int A, B, Am, Bp, Atp, Atm, Btp, Btm;
+};
+
+// One face.  The three sides are built one after the other, and only what a later
+// side needs is kept (the cell values and tangential slopes of A and B), so that few
+// values are live at once.
 template <class R, bool HALF>
-__device__ __forceinline__ void face_flux(const PhysT<R>& Q, const R* __restrict__ s, int RN, int kA,
-                                          int sn, int st, bool xface, R& Fh, R& Fp, R& Fmn, R& Fmt,
-                                          R& Fc) {
-    const int kB = kA + sn;
+__device__ __forceinline__ void face_flux(const PhysT<R>& Q, const R* __restrict__ s, int RN, const FaceCells& k,
+                                          bool xface, R& Fh, R& Fp, R& Fmn, R& Fmt, R& Fc) {
     const int fun = xface ? SU : SV, fut = xface ? SV : SU;
     const int qf[7] = {SP, fun, fut, SC, SMU, ST, SHE};
     const R dts = Q.dts;
-    // per primitive: A and B values, their tangential half-slopes, the mean of the two
-    // reconstructions at the face centre and half the mean tangential slope
-    R vA[7], hA[7], vB[7], hB[7], m0[7], hs[7], nA[7], nB[7];
-#pragma unroll
-    for (int q = 0; q < 7; ++q) {
-        const R* f = s + qf[q] * RN;
-        const R a = f[kA], b = f[kB];
-        const R na = R(0.5) * (b - f[kA - sn]);
-        const R nb = R(0.5) * (f[kB + sn] - a);
-        const R ta = R(0.5) * (f[kA + st] - f[kA - st]);
-        const R tb = R(0.5) * (f[kB + st] - f[kB - st]);
-        vA[q] = a;
-        vB[q] = b;
-        hA[q] = dts * ta;
-        hB[q] = dts * tb;
-        m0[q] = R(0.5) * (a + b) + R(0.25) * (na - nb);
-        hs[q] = R(0.5) * dts * (ta + tb);
-        if (!HALF) {
-            nA[q] = na;
-            nB[q] = nb;
-        }
-    }
-    const R FsA = s[SFS * RN + kA], FsB = s[SFS * RN + kB], Fsm = R(0.5) * (FsA + FsB);
+    const R FsA = s[SFS * RN + k.A], FsB = s[SFS * RN + k.B], Fsm = R(0.5) * (FsA + FsB);
     const R cpref = Q.cp_ref, Qg = Q.Q_g;
     const R rs = Q.rho_s, rl = Q.rho_l, rg = Q.rho_g, cs = Q.cp_s, cl = Q.cp_l, cg = Q.cp_g;
-    // Eq. 11 at fixed F_s is affine in C: rho = ra + rb C, C_p = ca + cb C on each side
-    const R rA0 = rg + FsA * (rs - rg), rA1 = (R(1) - FsA) * (rl - rg);
-    const R rB0 = rg + FsB * (rs - rg), rB1 = (R(1) - FsB) * (rl - rg);
-    const R rM0 = rg + Fsm * (rs - rg), rM1 = (R(1) - Fsm) * (rl - rg);
-    const R cA0 = cg + FsA * (cs - cg), cA1 = (R(1) - FsA) * (cl - cg);
-    const R cB0 = cg + FsB * (cs - cg), cB1 = (R(1) - FsB) * (cl - cg);
-    const R cM0 = cg + Fsm * (cs - cg), cM1 = (R(1) - Fsm) * (cl - cg);
-    // the centre point of each side's three points: the cell value, moved along the
-    // normal by (1/2 - dts) cells when the streaming step is not half a cell
-    R cAv[7], cBv[7];
-#pragma unroll
-    for (int k = 0; k < 7; ++k) {
-        cAv[k] = vA[k];
-        cBv[k] = vB[k];
-        if (!HALF) {
-            cAv[k] += (R(0.5) - dts) * nA[k];
-            cBv[k] += (R(-0.5) + dts) * nB[k];
-        }
-    }
     R Sp = 0, Sjn = 0, Sjt = 0, SC_ = 0, SH = 0, Ah = 0, Ag = 0, BGn = 0, BGt = 0;
-    side_sums<R, 1>(cAv, hA, rA0, rA1, cA0, cA1, cpref, Qg, Sp, Sjn, Sjt, SC_, SH, Ah, Ag, BGn, BGt);
-    side_sums<R, -1>(cBv, hB, rB0, rB1, cB0, cB1, cpref, Qg, Sp, Sjn, Sjt, SC_, SH, Ah, Ag, BGn, BGt);
-    side_sums<R, 0>(m0, hs, rM0, rM1, cM0, cM1, cpref, Qg, Sp, Sjn, Sjt, SC_, SH, Ah, Ag, BGn, BGt);
+    R a[6], b[6], ta[6], tb[6];
+    R pA, pB, hA0, hB0;
+    // side A: the three points with e_a.n = +1, reconstructed from A (Eq. 44)
+    {
+        R c[7], h[7];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const R* f = s + qf[q] * RN;
+            a[q] = f[k.A];
+            ta[q] = R(0.5) * (f[k.Atp] - f[k.Atm]);
+            h[q] = dts * ta[q];
+            c[q] = a[q];
+            // the centre point moves along the normal by (1/2 - dts) cells unless dts = 1/2
+            if (!HALF) c[q] += (R(0.5) - dts) * (R(0.5) * (f[k.B] - f[k.Am]));
+        }
+        c[6] = h[6] = R(0);
+        // Eq. 11 at fixed F_s is affine in C: rho = r0 + r1 C, C_p = c0 + c1 C
+        const R r0 = rg + FsA * (rs - rg), r1 = (R(1) - FsA) * (rl - rg);
+        const R k0 = cg + FsA * (cs - cg), k1 = (R(1) - FsA) * (cl - cg);
+        side_sums<R, 1>(c, h, r0, r1, k0, k1, cpref, Qg, Sp, Sjn, Sjt, SC_, SH, Ah, Ag, BGn, BGt);
+        pA = c[0];
+        hA0 = h[0];
+    }
+    // side B: e_a.n = -1, from B
+    {
+        R c[7], h[7];
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const R* f = s + qf[q] * RN;
+            b[q] = f[k.B];
+            tb[q] = R(0.5) * (f[k.Btp] - f[k.Btm]);
+            h[q] = dts * tb[q];
+            c[q] = b[q];
+            if (!HALF) c[q] += (R(-0.5) + dts) * (R(0.5) * (f[k.Bp] - f[k.A]));
+        }
+        c[6] = h[6] = R(0);
+        const R r0 = rg + FsB * (rs - rg), r1 = (R(1) - FsB) * (rl - rg);
+        const R k0 = cg + FsB * (cs - cg), k1 = (R(1) - FsB) * (cl - cg);
+        side_sums<R, -1>(c, h, r0, r1, k0, k1, cpref, Qg, Sp, Sjn, Sjt, SC_, SH, Ah, Ag, BGn, BGt);
+        pB = c[0];
+        hB0 = h[0];
+    }
+    // side M: e_a.n = 0, the mean of both cells' reconstructions at the face centre
+    // (and half the mean tangential slope)
+    const R rM0 = rg + Fsm * (rs - rg), rM1 = (R(1) - Fsm) * (rl - rg);
+    const R cM0 = cg + Fsm * (cs - cg), cM1 = (R(1) - Fsm) * (cl - cg);
+    {
+        R m0[7], hs[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            const R* f = s + qf[q] * RN;
+            const R av = q < 6 ? a[q] : f[k.A], bv = q < 6 ? b[q] : f[k.B];
+            const R na = R(0.5) * (bv - f[k.Am]);
+            const R nb = R(0.5) * (f[k.Bp] - av);
+            m0[q] = R(0.5) * (av + bv) + R(0.25) * (na - nb);
+            hs[q] = q < 6 ? R(0.5) * dts * (ta[q] + tb[q]) : R(0);
+        }
+        side_sums<R, 0>(m0, hs, rM0, rM1, cM0, cM1, cpref, Qg, Sp, Sjn, Sjt, SC_, SH, Ah, Ag, BGn, BGt);
+    }
     // sum over e_a.n != 0 of w_a p and of (e_a.n)(e_a.t) w_a p: the three points of a side
     // carry the weights 1/9, 1/36, 1/36 and sit at c, c - h, c + h along t
-    const R Bpn = R(1.0 / 6.0) * (cAv[0] + cBv[0]);
-    const R Bpt = R(1.0 / 18.0) * (hB[0] - hA[0]);
+    const R Bpn = R(1.0 / 6.0) * (pA + pB);
+    const R Bpt = R(1.0 / 18.0) * (hB0 - hA0);
     // Eq. 45: interface values
     const R Cf = SC_, pf = Sp, Hef = SH;
     const R rhof = rM0 + rM1 * Cf;
@@ -163,6 +186,21 @@ __device__ __forceinline__ void face_flux(const PhysT<R>& Q, const R* __restrict
     Fp = Sjn;
     Fmn = (R(1.5) - tau_f) * c3 * (pf + rhof * ufn * ufn) + (tau_f - R(0.5)) * (Bpn + rhof * c3 * BGn);
     Fmt = (R(1.5) - tau_f) * c3 * rhof * ufn * uft + (tau_f - R(0.5)) * (Bpt + rhof * c3 * BGt);
+}
+
+// the cells of an interior face in a region laid out with row stride st (x faces:
+// normal stride 1; y faces: normal stride st, tangential stride 1)
+__device__ __forceinline__ FaceCells region_face(int kA, int sn, int st) {
+    FaceCells k;
+    k.A = kA;
+    k.B = kA + sn;
+    k.Am = kA - sn;
+    k.Bp = kA + 2 * sn;
+    k.Atp = kA + st;
+    k.Atm = kA - st;
+    k.Btp = kA + sn + st;
+    k.Btm = kA + sn - st;
+    return k;
 }
 
 // Wall face (no-slip, no-flux): momentum flux c_s^2 (p n - mu du_t/dn) with the wall
@@ -474,7 +512,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
                 } else if (!P.periodic_x && gxf == nx) {
                     wall_flux<R>(Q, P.thermal_dir[1], s, RN, kA, 1, F);
                 } else {
-                    face_flux<R, HALF>(Q, s, RN, kA, 1, RW, true, F[0], F[1], F[2], F[3], F[4]);
+                    face_flux<R, HALF>(Q, s, RN, region_face(kA, 1, RW), true, F[0], F[1], F[2], F[3], F[4]);
                 }
             }
         } else {
@@ -490,7 +528,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
                 } else if (!P.periodic_y && gyf == ny) {
                     wall_flux<R>(Q, P.thermal_dir[3], s, RN, kA, 3, F);
                 } else {
-                    face_flux<R, HALF>(Q, s, RN, kA, RW, 1, false, F[0], F[1], F[3], F[2], F[4]);
+                    face_flux<R, HALF>(Q, s, RN, region_face(kA, RW, 1), false, F[0], F[1], F[3], F[2], F[4]);
                 }
             }
         }
@@ -660,6 +698,25 @@ struct StageShape {
     }
 };
 
+// Tile shapes the autotuner chooses from (id -> TX x TY cells per block, and the
+// number of blocks per SM the register budget is cut for in mixed precision: 1 for
+// ids 0-2, 2 for 3-4, 3 for 5-6, 4 for 7-10).  Ids 9 and 10 run 256 threads (one per
+// cell) instead of 288, which leaves 64 registers a thread at four blocks per SM.  All
+// have 256 or more cells, so a case never has more stage tiles than with 16 x 16.
+static constexpr int kShapes = 11;
+static constexpr int kShapeW[kShapes] = {32, 32, 64, 16, 64, 16, 32, 16, 32, 16, 32};
+static constexpr int kShapeH[kShapes] = {8, 16, 8, 16, 4, 16, 8, 16, 8, 16, 8};
+
+int stage_tile_shapes() { return kShapes; }
+int stage_tile_w(int prec, int tile) {
+    (void)prec;
+    return kShapeW[(tile >= 0 && tile < kShapes) ? tile : 0];
+}
+int stage_tile_h(int prec, int tile) {
+    (void)prec;
+    return kShapeH[(tile >= 0 && tile < kShapes) ? tile : 0];
+}
+
 // NT: threads per block (0: the shape's default, one thread per two faces)
 template <class R, class HR, int TX, int TY, int MINB, bool HALF, int NTB = 0>
 static cudaError_t launch_t(const DevCase* cases, const TileRef* tiles, int ntiles, int stage, cudaStream_t st) {
@@ -678,25 +735,6 @@ static cudaError_t launch_t(const DevCase* cases, const TileRef* tiles, int ntil
     }
     kern<<<ntiles, NT, sm, st>>>(cases, tiles, ntiles, stage);
     return cudaGetLastError();
-}
-
-// Tile shapes the autotuner chooses from (id -> TX x TY cells per block, and the
-// number of blocks per SM the register budget is cut for in mixed precision: 1 for
-// ids 0-2, 2 for 3-4, 3 for 5-6, 4 for 7-10).  Ids 9 and 10 run 256 threads (one per
-// cell) instead of 288, which leaves 64 registers a thread at four blocks per SM.  All
-// have 256 or more cells, so a case never has more stage tiles than with 16 x 16.
-static constexpr int kShapes = 11;
-static constexpr int kShapeW[kShapes] = {32, 32, 64, 16, 64, 16, 32, 16, 32, 16, 32};
-static constexpr int kShapeH[kShapes] = {8, 16, 8, 16, 4, 16, 8, 16, 8, 16, 8};
-
-int stage_tile_shapes() { return kShapes; }
-int stage_tile_w(int prec, int tile) {
-    (void)prec;
-    return kShapeW[(tile >= 0 && tile < kShapes) ? tile : 0];
-}
-int stage_tile_h(int prec, int tile) {
-    (void)prec;
-    return kShapeH[(tile >= 0 && tile < kShapes) ? tile : 0];
 }
 
 template <class R, int TX, int TY, int MINB, int NTB = 0>

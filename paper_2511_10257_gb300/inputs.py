@@ -101,7 +101,7 @@ class SplitMix64:
 
 
 def sweep_cases(n: int = 64, seed: int = 0, nx_min: int = 128, nx_max: int = 512,
-                nx_step: int = 32) -> list:
+                nx_step: int = 8) -> list:
     """The seeded batched sweep: grids drawn uniformly from nx_min x nx_min/2 to
     nx_max x nx_max/2 (nx a multiple of nx_step, ny = nx/2), droplet radius 0.375 ny,
     field angle uniform in [0, 90] degrees, Bo_m uniform in [0, 2], Stefan number

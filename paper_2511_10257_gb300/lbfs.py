@@ -36,7 +36,7 @@ class Config(ct.Structure):
                 ("use_graph", ct.c_int32), ("cuda_stream", ct.c_void_p),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", ct.c_void_p),
                 ("mg_max_cycles", ct.c_int32), ("mg_tol", ct.c_double), ("tile", ct.c_int32),
-                ("reserved", ct.c_int32 * 7)]
+                ("mg_warm_cycles", ct.c_int32), ("reserved", ct.c_int32 * 6)]
 
 
 class CaseDesc(ct.Structure):
@@ -64,7 +64,8 @@ class CaseStats(ct.Structure):
     _fields_ = [("sum_C", ct.c_double), ("sum_He", ct.c_double), ("sum_Fl_drop", ct.c_double),
                 ("n_drop", ct.c_double), ("Q_L", ct.c_double), ("t", ct.c_double),
                 ("t_freeze", ct.c_double), ("pot_resid", ct.c_double),
-                ("pot_cycles", ct.c_int32), ("nonfinite", ct.c_int32)]
+                ("pot_cycles", ct.c_int32), ("nonfinite", ct.c_int32),
+                ("pot_resid_max", ct.c_double), ("pot_cycles_mean", ct.c_double)]
 
 
 class CaseDiag(ct.Structure):
@@ -150,7 +151,7 @@ class Solver:
 
     def __init__(self, precision: int = FP64, max_cases: int = 1, device: int = 0,
                  use_graph: bool = False, stream=None, torch_alloc: bool = False,
-                 mg_max_cycles: int = 0, mg_tol: float = 0.0, tile: int = 0):
+                 mg_max_cycles: int = 0, mg_tol: float = 0.0, tile: int = 0, mg_warm_cycles: int = 0):
         self._L = load()
         self._h = ct.c_void_p()
         cfg = Config()
@@ -162,6 +163,7 @@ class Solver:
         cfg.mg_max_cycles = mg_max_cycles
         cfg.mg_tol = mg_tol
         cfg.tile = tile
+        cfg.mg_warm_cycles = mg_warm_cycles
         self._keep = []
         if torch_alloc:
             import torch
@@ -181,6 +183,11 @@ class Solver:
         self.max_cases = max_cases
         self.precision = precision
         self.shapes = {}
+        self._mg_tol = mg_tol
+
+    def mg_tol_used(self) -> float:
+        """the potential's convergence tolerance in effect (the library's default when 0)"""
+        return self._mg_tol if self._mg_tol > 0 else (1e-13 if self.precision == FP64 else 1e-6)
 
     def _check(self, st: int):
         if st != OK:

@@ -33,3 +33,24 @@ def assert_parity(solver, case_id, ref, tol, fields=ALL_FIELDS):
 def set_both(solver, case_id, ref, state):
     solver.set_fields(case_id, state)
     ref.set_state(state)
+
+
+def _oracle_job(job):
+    """worker of oracle_pool: (case, steps, fields, state) -> {field: array}"""
+    case, steps, fields, state = job
+    o = oracle.Oracle(case, threads=1)
+    if state:
+        o.set_state(state)
+    o.step(steps)
+    return {f: o.get(f) for f in fields}
+
+
+def oracle_pool(jobs, processes=None):
+    """Run independent oracle cases in parallel worker processes started with spawn
+    (safe after the CUDA context exists).  jobs: (case, steps, fields, state or None)."""
+    import multiprocessing as mp
+    import os
+    n = processes or min(len(jobs), os.cpu_count() or 1)
+    oracle.build()
+    with mp.get_context("spawn").Pool(n) as pool:
+        return pool.map(_oracle_job, jobs)

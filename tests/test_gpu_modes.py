@@ -129,3 +129,32 @@ def test_tile_shapes_give_identical_fields(precision):
     s.close()
     for f in IDS:
         assert np.array_equal(after[f], plain[f]), I.FIELD_NAMES[f]
+
+
+@pytest.mark.parametrize("precision", [lbfs.MIXED, lbfs.FP64])
+def test_every_warm_step_ends_converged(precision):
+    """Each step's potential solve ends with the residual of the corrected potential
+    at or below the tolerance, in eager steps and in graph replay."""
+    c = I.case(96, 48, radius=18.0, bo_m=1.5, field_angle_deg=60.0, stefan=0.3)
+    tol = 1e-6 if precision == lbfs.MIXED else 1e-13
+    for graph in (False, True):
+        s = lbfs.Solver(precision=precision, max_cases=1, use_graph=graph)
+        s.set_case(0, c)
+        s.step(1)
+        st = s.step(200)[0]
+        s.close()
+        assert 0.0 < st["pot_resid_max"] <= tol, st
+        assert st["pot_resid"] <= tol
+        assert st["pot_cycles_mean"] >= (1.0 if precision == lbfs.FP64 else 0.0)
+
+
+def test_warm_solve_reports_a_missed_tolerance():
+    """One warm cycle cannot take the mixed potential to 1e-13: lbfs_step says so."""
+    c = I.case(96, 48, radius=18.0, bo_m=1.5, field_angle_deg=60.0, stefan=0.3)
+    s = lbfs.Solver(precision=lbfs.MIXED, max_cases=1, mg_tol=1e-13, mg_warm_cycles=1)
+    s.set_case(0, c)
+    s.step(1)
+    status, st = s.step(5, raise_on_error=False)
+    s.close()
+    assert status == lbfs.ENOTCONVERGED
+    assert st[0]["pot_resid_max"] > 1e-13
