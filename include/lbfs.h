@@ -71,7 +71,11 @@ typedef struct lbfs_config {
                                 so these steps need no host round trip and can be replayed
                                 as a CUDA graph.  A residual still above mg_tol after the
                                 last cycle makes lbfs_step return LBFS_ENOTCONVERGED     */
-    int32_t reserved[6];
+    int32_t mg_plain_cycles; /* 1: launch those cycles as mg_warm_cycles plain rounds of
+                                kernels, each returning at once for a converged case,
+                                instead of a conditional graph loop (kernel profilers
+                                cannot follow conditional graph nodes); same results     */
+    int32_t reserved[5];
 } lbfs_config;
 
 /* One case.  Walls are numbered 0 left (x = 0), 1 right (x = nx), 2 bottom (y = 0),

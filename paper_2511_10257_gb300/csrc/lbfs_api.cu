@@ -460,6 +460,22 @@ lbfs_status potential_solve(lbfs_ctx* ctx) {
     if (ctx->n_pot == 0) return LBFS_OK;
     const int p = ctx->prec;
     cudaStream_t s = ctx->stream;
+    if (!ctx->pot_fresh && ctx->cfg.mg_plain_cycles) {
+        // the same cycles as plain launches; each kernel returns at once for a converged case
+        const int K = ctx->mg_warm_cycles;
+        int* nd = ctx->d_flag + 1;
+        LK(launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], 1, s));
+        LK(launch_mg_finalize(p, ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, 1, K, nd, nullptr, 0, 0, s));
+        for (int c = 0; c < K; ++c) {
+            lbfs_status r = vcycle(ctx);
+            if (r != LBFS_OK) return r;
+            LK(launch_mg_correct(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], s));
+            LK(launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], 0, s));
+            LK(launch_mg_finalize(p, ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, 0, K, nd, nullptr, 0, 0, s));
+        }
+        CK(cudaMemsetAsync(nd, 0, sizeof(int), s));
+        return LBFS_OK;
+    }
     if (!ctx->pot_fresh) {
         if (ctx->capturing) return capture_warm_potential(ctx);
         if (!ctx->pot_exec) {
@@ -849,7 +865,7 @@ lbfs_status lbfs_step(lbfs_ctx* ctx, int32_t nsteps, lbfs_case_stats* out) {
     CK(cudaMemcpyAsync(ctx->h_stats, ctx->d_stats, nb, cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     harvest(ctx);
-    if (ctx->n_pot > 0 && ctx->cycle_launches > 0) {
+    if (ctx->n_pot > 0 && ctx->cycle_launches > 0 && !ctx->cfg.mg_plain_cycles) {
         // refinement cycles run by device-decided loops: at least the most any case ran
         double cyc = 0.0;
         for (size_t c = 0; c < ctx->slots.size(); ++c)

@@ -36,7 +36,7 @@ class Config(ct.Structure):
                 ("use_graph", ct.c_int32), ("cuda_stream", ct.c_void_p),
                 ("dev_alloc", ALLOC_FN), ("dev_free", FREE_FN), ("alloc_user", ct.c_void_p),
                 ("mg_max_cycles", ct.c_int32), ("mg_tol", ct.c_double), ("tile", ct.c_int32),
-                ("mg_warm_cycles", ct.c_int32), ("reserved", ct.c_int32 * 6)]
+                ("mg_warm_cycles", ct.c_int32), ("mg_plain_cycles", ct.c_int32), ("reserved", ct.c_int32 * 5)]
 
 
 class CaseDesc(ct.Structure):
@@ -151,7 +151,8 @@ class Solver:
 
     def __init__(self, precision: int = FP64, max_cases: int = 1, device: int = 0,
                  use_graph: bool = False, stream=None, torch_alloc: bool = False,
-                 mg_max_cycles: int = 0, mg_tol: float = 0.0, tile: int = 0, mg_warm_cycles: int = 0):
+                 mg_max_cycles: int = 0, mg_tol: float = 0.0, tile: int = 0, mg_warm_cycles: int = 0,
+                 mg_plain_cycles: bool = False):
         self._L = load()
         self._h = ct.c_void_p()
         cfg = Config()
@@ -164,6 +165,7 @@ class Solver:
         cfg.mg_tol = mg_tol
         cfg.tile = tile
         cfg.mg_warm_cycles = mg_warm_cycles
+        cfg.mg_plain_cycles = 1 if mg_plain_cycles else 0
         self._keep = []
         if torch_alloc:
             import torch

@@ -158,3 +158,22 @@ def test_warm_solve_reports_a_missed_tolerance():
     s.close()
     assert status == lbfs.ENOTCONVERGED
     assert st[0]["pot_resid_max"] > 1e-13
+
+
+@pytest.mark.parametrize("precision", [lbfs.MIXED, lbfs.FP64])
+def test_plain_cycle_launches_give_identical_fields(precision):
+    """The warm cycles as a conditional graph loop or as plain launches are the same
+    computation: bitwise-identical fields, eager and replayed."""
+    c = I.case(96, 48, radius=18.0, bo_m=1.5, field_angle_deg=60.0, stefan=0.3)
+    out = []
+    for plain in (False, True):
+        for graph in (False, True):
+            s = lbfs.Solver(precision=precision, max_cases=1, use_graph=graph, mg_plain_cycles=plain)
+            s.set_case(0, c)
+            st = s.step(40)[0]
+            out.append((s.fields(0, IDS), st))
+            s.close()
+    for got, st in out[1:]:
+        for f in IDS:
+            assert np.array_equal(got[f], out[0][0][f]), I.FIELD_NAMES[f]
+        assert st["pot_resid_max"] == out[0][1]["pot_resid_max"]
