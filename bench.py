@@ -54,6 +54,8 @@ def workloads():
                   I.config_large()),
         "medium": ("512x256 sessile ferrofluid drop, R=96, vertical field, Bo_m=1.0, chi=1, Ste=0.1",
                    I.config_medium()),
+        "small": ("128x64 sessile ferrofluid drop, R=24, vertical field, Bo_m=0.5, chi=1, Ste=0.1",
+                  I.config_small()),
         "batch": ("64-case seeded sweep (SplitMix64 seed 0): grids 128x64..512x256, R=0.375 ny, "
                   "field angle 0-90 deg, Bo_m 0-2, Ste 0.05-0.2, chi=1", I.sweep_cases(64, 0)),
     }
@@ -220,12 +222,29 @@ def run_reference(args):
         return 0
     import oracle
     oracle.build()
-    name, case = workloads()[args.workload]
-    sample = sample_case(case, args.sample_factor)
-    threads = os.cpu_count() or 1
-    value, dt = oracle_rate(sample, args.steps, args.warmup, threads)
-    sample_desc = (f"the {name} physics on a {sample['nx']}x{sample['ny']} grid (R={sample['radius']:g}), "
-                   f"{args.steps} steps after {args.warmup} warm-up steps, {threads} OpenMP threads")
+    name, work = workloads()[args.workload]
+    threads = args.threads if args.threads > 0 else (os.cpu_count() or 1)
+    if isinstance(work, list):
+        # the sweep: its first cases, each advanced the full step count
+        sub = work[:args.ref_cases]
+        ncs = sum(c["nx"] * c["ny"] for c in sub)
+        t0 = time.perf_counter()
+        for c in sub:
+            oracle_rate(c, args.steps, args.warmup, threads)
+        dt = time.perf_counter() - t0
+        value = ncs * args.steps / dt / 1e6
+        case = work[0]
+        sample_desc = (f"the first {len(sub)} cases of the sweep ({ncs} cells), {args.steps} steps each after "
+                       f"{args.warmup} warm-up steps, {threads} OpenMP threads")
+    else:
+        case = work
+        # grids up to 512x256 run whole; larger ones on a grid coarser by sample_factor
+        factor = 1 if case["nx"] * case["ny"] <= 512 * 256 else args.sample_factor
+        sample = sample_case(case, factor)
+        value, dt = oracle_rate(sample, args.steps, args.warmup, threads)
+        what = "the workload itself" if factor == 1 else (
+            f"the {name} physics on a {sample['nx']}x{sample['ny']} grid (R={sample['radius']:g})")
+        sample_desc = (f"{what}, {args.steps} steps after {args.warmup} warm-up steps, {threads} OpenMP threads")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
@@ -233,7 +252,7 @@ def run_reference(args):
         "data": "synthetic", "config": {"workload": name, "grid": f"{case['nx']}x{case['ny']}",
                                         "sample": sample_desc},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
-                         "sample": sample_desc},
+                         "cpu": cpu_model(), "sample": sample_desc},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -491,11 +510,14 @@ def main(argv=None):
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="huge", choices=["huge", "large", "medium", "batch"])
+    ap.add_argument("--workload", default="huge", choices=["huge", "large", "medium", "small", "batch"])
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--fp64-steps", type=int, default=5)
     ap.add_argument("--cpu-steps", type=int, default=20, help="oracle steps per case of the batch baseline")
-    ap.add_argument("--sample-factor", type=int, default=16)
+    ap.add_argument("--sample-factor", type=int, default=16,
+                    help="reference arm: grids above 512x256 are timed on a grid this much coarser")
+    ap.add_argument("--threads", type=int, default=0, help="reference arm: oracle threads (0: all cores)")
+    ap.add_argument("--ref-cases", type=int, default=8, help="reference arm, sweep: cases timed")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-potential-compare", action="store_true",

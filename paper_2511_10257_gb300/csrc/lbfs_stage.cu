@@ -94,6 +94,92 @@ struct FaceCells {
 // One face.  The three sides are built one after the other, and only what a later
 // side needs is kept (the cell values and tangential slopes of A and B), so that few
 // values are live at once.
+// ---- packed FP32: two lanes per instruction (Blackwell FADD2 / FMUL2 / FFMA2) ----
+__device__ __forceinline__ float2 sp2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __fadd2_rn(a, make_float2(-b.x, -b.y)); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Sides A (e_a.n = +1, lane x) and B (e_a.n = -1, lane y) of a face together, as packed
+// FP32: the same point equilibria as side_sums<float, +1> and <float, -1>, two sides per
+// instruction.  c, h: the cell values and tangential half-slopes of A (x) and B (y);
+// r0 + r1 C and k0 + k1 C: Eq. 11 for rho and C_p on each side.
+__device__ __forceinline__ void side_sums_ab(const float2 c[6], const float2 h[6], float2 r0, float2 r1, float2 k0,
+                                             float2 k1, float cpref, float Qg, float& Sp, float& Sjn, float& Sjt,
+                                             float& SC_, float& SH, float& Ah, float& Ag, float& BGn, float& BGt) {
+    const float2 sg = make_float2(1.f, -1.f);
+    float2 F[3], Gm[3], Hh[3], Ga[3];
+#pragma unroll
+    for (int e = 0; e < 3; ++e) {
+        const int et = e == 0 ? 0 : (e == 1 ? 1 : -1);
+        float2 q[6];
+#pragma unroll
+        for (int k = 0; k < 6; ++k) q[k] = et == 0 ? c[k] : (et > 0 ? sub2(c[k], h[k]) : add2(c[k], h[k]));
+        const float2 p = q[0], un = q[1], ut = q[2], C = q[3], mu = q[4], T = q[5];
+        const float2 rho = fma2(r1, C, r0), cp = fma2(k1, C, k0);
+        const float2 eu = et == 0 ? mul2(sg, un) : (et > 0 ? fma2(sg, un, ut) : fma2(sg, un, make_float2(-ut.x, -ut.y)));
+        const float2 uu = fma2(un, un, mul2(ut, ut));
+        const float2 G = fma2(sp2(-1.5f), uu, mul2(eu, fma2(sp2(4.5f), eu, sp2(3.f))));   // Gamma_a(u)
+        F[e] = fma2(mul2(rho, G), sp2(1.f / 3.f), p);
+        Gm[e] = G;
+        Hh[e] = mul2(T, fma2(cp, G, sp2(cpref)));
+        Ga[e] = fma2(C, eu, mul2(mu, sp2(Qg)));
+    }
+    const float w0 = 1.f / 9.f, w1 = 1.f / 36.f;
+    const float2 F12 = add2(F[1], F[2]);
+    const float2 Fs = fma2(sp2(w0), F[0], mul2(sp2(w1), F12));
+    const float2 gs = mul2(sp2(3.f), fma2(sp2(w0), Ga[0], mul2(sp2(w1), add2(Ga[1], Ga[2]))));
+    const float2 hs = fma2(sp2(w0), Hh[0], mul2(sp2(w1), add2(Hh[1], Hh[2])));
+    const float2 bg = fma2(sp2(w0), Gm[0], mul2(sp2(w1), add2(Gm[1], Gm[2])));
+    const float2 dF = mul2(sp2(w1), sub2(F[1], F[2]));
+    const float2 dG = mul2(sp2(w1), sub2(Gm[1], Gm[2]));
+    Sp += Fs.x + Fs.y;
+    Sjn += Fs.x - Fs.y;
+    Sjt += dF.x + dF.y;
+    SC_ += gs.x + gs.y;
+    Ag += gs.x - gs.y;
+    SH += hs.x + hs.y;
+    Ah += hs.x - hs.y;
+    BGn += bg.x + bg.y;
+    BGt += dG.x - dG.y;
+}
+
+// The rest side (e_a.n = 0) in packed FP32: its centre point (the rest direction) in
+// scalar form, its two tangential points c - h (e_a.t = +1, lane x) and c + h
+// (e_a.t = -1, lane y) as two lanes; the same equilibria as side_sums<float, 0>.
+__device__ __forceinline__ void side_sums_rest2(const float c[7], const float h[7], float r0, float r1, float k0,
+                                                float k1, float cpref, float Qg, float& Sp, float& Sjt, float& SC_,
+                                                float& SH, float& BGn) {
+    const float w0 = 4.f / 9.f, w1 = 1.f / 9.f;
+    // centre: e_a = 0, so e.u = 0
+    const float uu0 = c[1] * c[1] + c[2] * c[2];
+    const float G0 = -1.5f * uu0;
+    const float rho0 = r0 + r1 * c[3], cp0 = k0 + k1 * c[3];
+    const float F0 = c[0] + rho0 * G0 * (1.f / 3.f);
+    const float Hh0 = c[5] * (cpref + cp0 * G0);
+    // the tangential pair
+    float2 q[6];
+#pragma unroll
+    for (int k = 0; k < 6; ++k) q[k] = make_float2(c[k] - h[k], c[k] + h[k]);
+    const float2 un = q[1], ut = q[2], C = q[3];
+    const float2 eu = make_float2(ut.x, -ut.y);
+    const float2 rho = fma2(sp2(r1), C, sp2(r0)), cp = fma2(sp2(k1), C, sp2(k0));
+    const float2 uu = fma2(un, un, mul2(ut, ut));
+    const float2 G = fma2(sp2(-1.5f), uu, mul2(eu, fma2(sp2(4.5f), eu, sp2(3.f))));
+    const float2 F = fma2(mul2(rho, G), sp2(1.f / 3.f), q[0]);
+    const float2 Hh = mul2(q[5], fma2(cp, G, sp2(cpref)));
+    const float2 Ga = fma2(C, eu, mul2(q[4], sp2(Qg)));
+    // a = 0: g_eq = C - (5/3) mu Q_g, h_eq = H_e - C_p,ref T + w0 T (C_p,ref + C_p Gamma)
+    const float geq0 = c[3] - (5.f / 3.f) * c[4] * Qg;
+    const float heq0 = c[6] - cpref * c[5] + w0 * Hh0;
+    Sp += w0 * F0 + w1 * (F.x + F.y);
+    Sjt += w1 * (F.x - F.y);
+    SC_ += geq0 + 3.f * w1 * (Ga.x + Ga.y);
+    SH += heq0 + w1 * (Hh.x + Hh.y);
+    (void)BGn;
+}
+
 template <class R, bool HALF>
 __device__ __forceinline__ void face_flux(const PhysT<R>& Q, const R* __restrict__ s, int RN, const FaceCells& k,
                                           bool xface, R& Fh, R& Fp, R& Fmn, R& Fmt, R& Fc) {
@@ -106,6 +192,34 @@ __device__ __forceinline__ void face_flux(const PhysT<R>& Q, const R* __restrict
     R Sp = 0, Sjn = 0, Sjt = 0, SC_ = 0, SH = 0, Ah = 0, Ag = 0, BGn = 0, BGt = 0;
     R a[6], b[6], ta[6], tb[6];
     R pA, pB, hA0, hB0;
+    if constexpr (sizeof(R) == 4) {
+        // sides A (e_a.n = +1, from A) and B (e_a.n = -1, from B), two lanes of packed FP32
+        float2 c[6], h[6];
+        const float2 dt2 = sp2(dts);
+#pragma unroll
+        for (int q = 0; q < 6; ++q) {
+            const R* f = s + qf[q] * RN;
+            a[q] = f[k.A];
+            b[q] = f[k.B];
+            const float2 t = mul2(sp2(0.5f), sub2(make_float2(f[k.Atp], f[k.Btp]), make_float2(f[k.Atm], f[k.Btm])));
+            ta[q] = t.x;
+            tb[q] = t.y;
+            h[q] = mul2(dt2, t);
+            c[q] = make_float2(a[q], b[q]);
+            // the centre point moves along the normal by (1/2 - dts) cells unless dts = 1/2
+            if (!HALF)
+                c[q] = fma2(make_float2(R(0.5) - dts, R(-0.5) + dts),
+                            mul2(sp2(0.5f), make_float2(f[k.B] - f[k.Am], f[k.Bp] - f[k.A])), c[q]);
+        }
+        const float2 Fs2 = make_float2(FsA, FsB);
+        const float2 r0 = fma2(Fs2, sp2(rs - rg), sp2(rg)), r1 = mul2(sub2(sp2(1.f), Fs2), sp2(rl - rg));
+        const float2 k0 = fma2(Fs2, sp2(cs - cg), sp2(cg)), k1 = mul2(sub2(sp2(1.f), Fs2), sp2(cl - cg));
+        side_sums_ab(c, h, r0, r1, k0, k1, cpref, Qg, Sp, Sjn, Sjt, SC_, SH, Ah, Ag, BGn, BGt);
+        pA = c[0].x;
+        pB = c[0].y;
+        hA0 = h[0].x;
+        hB0 = h[0].y;
+    } else {
     // side A: the three points with e_a.n = +1, reconstructed from A (Eq. 44)
     {
         R c[7], h[7];
@@ -146,6 +260,7 @@ __device__ __forceinline__ void face_flux(const PhysT<R>& Q, const R* __restrict
         pB = c[0];
         hB0 = h[0];
     }
+    }
     // side M: e_a.n = 0, the mean of both cells' reconstructions at the face centre
     // (and half the mean tangential slope)
     const R rM0 = rg + Fsm * (rs - rg), rM1 = (R(1) - Fsm) * (rl - rg);
@@ -156,12 +271,15 @@ __device__ __forceinline__ void face_flux(const PhysT<R>& Q, const R* __restrict
         for (int q = 0; q < 7; ++q) {
             const R* f = s + qf[q] * RN;
             const R av = q < 6 ? a[q] : f[k.A], bv = q < 6 ? b[q] : f[k.B];
-            const R na = R(0.5) * (bv - f[k.Am]);
-            const R nb = R(0.5) * (f[k.Bp] - av);
-            m0[q] = R(0.5) * (av + bv) + R(0.25) * (na - nb);
+            // (a + b)/2 + ((b - a_m) - (b_p - a))/8: the mean of the two cells' linear
+            // reconstructions at the face centre
+            m0[q] = R(0.625) * (av + bv) - R(0.125) * (f[k.Am] + f[k.Bp]);
             hs[q] = q < 6 ? R(0.5) * dts * (ta[q] + tb[q]) : R(0);
         }
-        side_sums<R, 0>(m0, hs, rM0, rM1, cM0, cM1, cpref, Qg, Sp, Sjn, Sjt, SC_, SH, Ah, Ag, BGn, BGt);
+        if constexpr (sizeof(R) == 4)
+            side_sums_rest2(m0, hs, rM0, rM1, cM0, cM1, cpref, Qg, Sp, Sjt, SC_, SH, BGn);
+        else
+            side_sums<R, 0>(m0, hs, rM0, rM1, cM0, cM1, cpref, Qg, Sp, Sjn, Sjt, SC_, SH, Ah, Ag, BGn, BGt);
     }
     // sum over e_a.n != 0 of w_a p and of (e_a.n)(e_a.t) w_a p: the three points of a side
     // carry the weights 1/9, 1/36, 1/36 and sit at c, c - h, c + h along t
@@ -361,7 +479,10 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
 
     // ---- phase 1: load the stage state with halo, ghost rules at walls ----------
     // All of a thread's region loads are issued before any is used (one memory latency
-    // per tile instead of one per region cell of the thread).
+    // per tile instead of one per region cell of the thread).  An interior tile, whose
+    // region lies inside the grid, has no ghost and no wrap: its region cell (lx, ly)
+    // is the grid cell (x0 - H + lx, y0 - H + ly).
+    const bool interior = x0 >= Gm::H && x0 + TX + Gm::H <= nx && y0 >= Gm::H && y0 + TY + Gm::H <= ny;
     constexpr int ROUNDS = (RN + NT - 1) / NT;
     HR lHe[ROUNDS];
     R lC[ROUNDS], lP[ROUNDS], lMx[ROUNDS], lMy[ROUNDS], lPhi[ROUNDS];
@@ -373,6 +494,18 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         if (k >= RN) break;
         const int lx = k % RW, ly = k / RW;
         const int gx = x0 - Gm::H + lx, gy = y0 - Gm::H + ly;
+        if (interior) {
+            const size_t gi = (size_t)gy * pitch + gx;
+            lGi[i] = gi;
+            lWall[i] = -1;
+            lHe[i] = gHe[gi];
+            lC[i] = gC[gi];
+            lP[i] = gP[gi];
+            lMx[i] = gMx[gi];
+            lMy[i] = gMy[gi];
+            lPhi[i] = gPhi[gi];
+            continue;
+        }
         int sx, sy, xs, ys;  // source cell and status: 0 inside, 1 ghost low, 2 ghost high, 3 far
         if (per_x) {
             sx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
@@ -468,7 +601,23 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
     __syncthreads();
     // ---- phase 2: mu_c and |H|^2 at inner cells; a wall ghost takes the values of
     // the inner cell it mirrors (computed there again rather than copied, which saves
-    // a barrier) -------------------------------------------------------------------
+    // a barrier).  The faces and sources read mu_c and |H|^2 no further than two cells
+    // from the tile, so an interior tile computes them on that (RW-2) x (RH-2) core
+    // only, with no ghost to resolve. -------------------------------------------------
+    if (interior) {
+        constexpr int CW = RW - 2, CN = (RW - 2) * (RH - 2);
+        for (int t = threadIdx.x; t < CN; t += NT) {
+            const int k = (1 + t / CW) * RW + 1 + t % CW;
+            const R* c = s + SC * RN;
+            const R C = c[k];
+            const R lap = (c[k + 1] + c[k - 1]) + (c[k + RW] + c[k - RW]) - R(4) * C;
+            s[SMU * RN + k] = R(2) * Q.beta * C * (C - R(1)) * (R(2) * C - R(1)) - Q.kappa * lap;
+            const R* ph = s + SPHI * RN;
+            const R hx = R(-0.5) * (ph[k + 1] - ph[k - 1]);
+            const R hy = R(-0.5) * (ph[k + RW] - ph[k - RW]);
+            s[SH2 * RN + k] = hx * hx + hy * hy;
+        }
+    } else
     for (int k = threadIdx.x; k < RN; k += NT) {
         const int kd = kind[k];
         int kk = k;
@@ -700,12 +849,14 @@ struct StageShape {
 
 // Tile shapes the autotuner chooses from (id -> TX x TY cells per block, and the
 // number of blocks per SM the register budget is cut for in mixed precision: 1 for
-// ids 0-2, 2 for 3-4, 3 for 5-6, 4 for 7-10).  Ids 9 and 10 run 256 threads (one per
-// cell) instead of 288, which leaves 64 registers a thread at four blocks per SM.  All
-// have 256 or more cells, so a case never has more stage tiles than with 16 x 16.
-static constexpr int kShapes = 11;
-static constexpr int kShapeW[kShapes] = {32, 32, 64, 16, 64, 16, 32, 16, 32, 16, 32};
-static constexpr int kShapeH[kShapes] = {8, 16, 8, 16, 4, 16, 8, 16, 8, 16, 8};
+// ids 0-2, 2 for 3-4, 3 for 5-6, 4 for 7-12).  Ids 9-12 run 256 threads instead of
+// 288, which leaves 64 registers a thread at four blocks per SM.  Ids 11 (16 x 15) and
+// 12 (32 x 7) are cut so that the halo load and the faces each split into two even
+// rounds of 256 threads (the 16 x 16 and 32 x 8 tiles leave a small third round of
+// faces or halo cells for one warp while the others wait at the barrier).
+static constexpr int kShapes = 13;
+static constexpr int kShapeW[kShapes] = {32, 32, 64, 16, 64, 16, 32, 16, 32, 16, 32, 16, 32};
+static constexpr int kShapeH[kShapes] = {8, 16, 8, 16, 4, 16, 8, 16, 8, 16, 8, 15, 7};
 
 int stage_tile_shapes() { return kShapes; }
 int stage_tile_w(int prec, int tile) {
@@ -761,6 +912,8 @@ static cudaError_t launch_prec(int tile, int half, const DevCase* cases, const T
     case 8: return launch_h<R, 32, 8, MINB4>(half, cases, tiles, ntiles, stage, st);
     case 9: return launch_h<R, 16, 16, MINB4, 256>(half, cases, tiles, ntiles, stage, st);
     case 10: return launch_h<R, 32, 8, MINB4, 256>(half, cases, tiles, ntiles, stage, st);
+    case 11: return launch_h<R, 16, 15, MINB4, 256>(half, cases, tiles, ntiles, stage, st);
+    case 12: return launch_h<R, 32, 7, MINB4, 256>(half, cases, tiles, ntiles, stage, st);
     default: return launch_h<R, 32, 8, 1>(half, cases, tiles, ntiles, stage, st);
     }
 }

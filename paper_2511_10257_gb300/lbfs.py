@@ -77,9 +77,9 @@ EXPORTS = ("lbfs_create", "lbfs_set_case", "lbfs_set_fields", "lbfs_step", "lbfs
            "lbfs_diagnostics", "lbfs_potential_pseudo_time", "lbfs_last_launch_count", "lbfs_timing", "lbfs_timing_read", "lbfs_autotune",
            "lbfs_destroy", "lbfs_last_error")
 TILE_SHAPES = [(32, 8), (32, 16), (64, 8), (16, 16), (64, 4), (16, 16), (32, 8), (16, 16), (32, 8), (16, 16),
-               (32, 8)]
+               (32, 8), (16, 15), (32, 7)]
 TILE_NAMES = ["32x8", "32x16", "64x8", "16x16", "64x4", "16x16/3", "32x8/3", "16x16/4", "32x8/4", "16x16/4t",
-              "32x8/4t"]
+              "32x8/4t", "16x15/4t", "32x7/4t"]
 TIMING_STAGE, TIMING_POTENTIAL, TIMING_FINALIZE = range(3)
 
 _lib = None
