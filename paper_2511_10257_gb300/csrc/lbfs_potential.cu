@@ -691,6 +691,105 @@ __global__ void __launch_bounds__(256) k_coarsest(const DevCase* __restrict__ ca
     }
 }
 
+// The same solve by one warp per case, for coarsest levels of up to kCoarsestWarp
+// cells: the operator's coefficients are formed once, and an iteration's two sums are
+// warp shuffles, with no block-wide barrier.  Each iteration is a few hundred cycles
+// instead of the block version's six barriers.
+constexpr int kCoarsestWarp = 1024;
+
+template <class M>
+__device__ __forceinline__ M warp_allsum(M v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <class M>
+__global__ void __launch_bounds__(32) k_coarsest_warp(const DevCase* __restrict__ cases,
+                                                      const int* __restrict__ ids) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const DevCase* dc = cases + ids[blockIdx.x];
+    if (pot_done(dc)) return;
+    const CaseParams& P = dc->P;
+    const MGLevel lv = dc->lev[dc->nlev - 1];
+    const int nx = lv.nx, ny = lv.ny, n = nx * ny;
+    const int lane = threadIdx.x;
+    // x, r, p, A p, the diagonal and the four off-diagonal coefficients per cell, then
+    // the four neighbour indices (a wall side points at the cell itself with a zero
+    // coefficient)
+    M* x = reinterpret_cast<M*>(smem_raw);
+    M* r = x + n;
+    M* p = r + n;
+    M* Ap = p + n;
+    M* dg = Ap + n;
+    M* cw = dg + n;                                        // [4][n]
+    short* nb = reinterpret_cast<short*>(cw + 4 * n);       // [4][n]
+    const M* gmu = static_cast<const M*>(lv.mu);
+    M rr = 0;
+    for (int k = lane; k < n; k += 32) {
+        const int i = k % nx, j = k / nx;
+        const M mc = gmu[(size_t)j * lv.pitch + i];
+        M d = 0;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            int ii, jj;
+            M c = 0;
+            int kn = k;
+            if (neighbour(P, nx, ny, i, j, w, ii, jj)) {
+                kn = jj * nx + ii;
+                c = M(0.5) * (mc + gmu[(size_t)jj * lv.pitch + ii]);
+                if (lv.ragged) c *= face_factor<M>(lv, i, j, w, false);
+                d += c;
+            } else if (P.mag_dir[w]) {
+                d += (lv.ragged ? face_factor<M>(lv, i, j, w, true) : M(2)) * mc;
+            }
+            cw[w * n + k] = c;
+            nb[w * n + k] = (short)kn;
+        }
+        dg[k] = d;
+        const M rk = static_cast<const M*>(lv.r)[(size_t)j * lv.pitch + i];
+        r[k] = rk;
+        p[k] = rk;
+        x[k] = 0;
+        rr += rk * rk;
+    }
+    rr = warp_allsum(rr);
+    __syncwarp();
+    const M rr0 = rr;
+    // the same stopping rule as the block version
+    const M tol2 = sizeof(M) == 8 ? M(1e-28) : M(1e-6);
+    const int maxit = 4 * (nx + ny) + 100;
+    for (int it = 0; it < maxit && rr > tol2 * rr0 && rr > M(0); ++it) {
+        M pAp = 0;
+        for (int k = lane; k < n; k += 32) {
+            M a = dg[k] * p[k];
+#pragma unroll
+            for (int w = 0; w < 4; ++w) a -= cw[w * n + k] * p[nb[w * n + k]];
+            Ap[k] = a;
+            pAp += p[k] * a;
+        }
+        pAp = warp_allsum(pAp);
+        const M alpha = rr / pAp;
+        M rn = 0;
+        for (int k = lane; k < n; k += 32) {
+            x[k] += alpha * p[k];
+            const M rk = r[k] - alpha * Ap[k];
+            r[k] = rk;
+            rn += rk * rk;
+        }
+        rn = warp_allsum(rn);
+        const M beta = rn / rr;
+        rr = rn;
+        __syncwarp();   // every lane's reads of p for A p are done
+        for (int k = lane; k < n; k += 32) p[k] = r[k] + beta * p[k];
+        __syncwarp();
+    }
+    for (int k = lane; k < n; k += 32) {
+        const int i = k % nx, j = k / nx;
+        static_cast<M*>(lv.e)[(size_t)j * lv.pitch + i] = x[k];
+    }
+}
+
 template <class M>
 __global__ void __launch_bounds__(kNT) k_correct(const DevCase* __restrict__ cases,
                                                  const TileRef* __restrict__ tiles) {
@@ -868,22 +967,37 @@ cudaError_t launch_mg_vup(int prec, const DevCase* cases, const TileRef* tiles, 
 }
 
 size_t mg_coarsest_smem(int prec, int max_cells) {
-    return (size_t)5 * max_cells * (prec == 0 ? sizeof(double) : sizeof(float));
+    const size_t m = prec == 0 ? sizeof(double) : sizeof(float);
+    if (max_cells <= kCoarsestWarp) return (size_t)9 * max_cells * m + (size_t)4 * max_cells * sizeof(short);
+    return (size_t)5 * max_cells * m;
 }
 
 cudaError_t launch_mg_coarsest(int prec, const DevCase* cases, const int* ids, int ncases,
                                int max_cells, cudaStream_t st) {
     if (ncases <= 0) return cudaSuccess;
     const size_t sm = mg_coarsest_smem(prec, max_cells);
+    const bool warp = max_cells <= kCoarsestWarp;
     cudaError_t e;
     if (prec == 0) {
-        e = cudaFuncSetAttribute(k_coarsest<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        k_coarsest<double><<<ncases, 256, sm, st>>>(cases, ids);
+        if (warp) {
+            e = cudaFuncSetAttribute(k_coarsest_warp<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            k_coarsest_warp<double><<<ncases, 32, sm, st>>>(cases, ids);
+        } else {
+            e = cudaFuncSetAttribute(k_coarsest<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            k_coarsest<double><<<ncases, 256, sm, st>>>(cases, ids);
+        }
     } else {
-        e = cudaFuncSetAttribute(k_coarsest<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        if (e != cudaSuccess) return e;
-        k_coarsest<float><<<ncases, 256, sm, st>>>(cases, ids);
+        if (warp) {
+            e = cudaFuncSetAttribute(k_coarsest_warp<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            k_coarsest_warp<float><<<ncases, 32, sm, st>>>(cases, ids);
+        } else {
+            e = cudaFuncSetAttribute(k_coarsest<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            k_coarsest<float><<<ncases, 256, sm, st>>>(cases, ids);
+        }
     }
     return cudaGetLastError();
 }

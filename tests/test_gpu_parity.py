@@ -90,6 +90,19 @@ def test_potential_solve_matches(solver_fp64):
     assert_parity(solver_fp64, 0, ref, 1e-11, fields=[I.PHI])
 
 
+def test_potential_solve_large_coarsest_level(solver_fp64):
+    """a periodic axis that halves to an odd size at once leaves a coarsest level of
+    2060 cells, above the one-warp conjugate-gradient limit: the block-wide solve"""
+    c = I.case(1030, 8, periodic_x=1, radius=3.0, bo_m=2.0, field_angle_deg=30.0,
+               chi_l=2.0, chi_s=2.0)
+    ref = oracle.Oracle(c)
+    solver_fp64.set_case(0, c)
+    ref.step(1)
+    stats = solver_fp64.step(1)[0]
+    assert stats["pot_resid"] <= 1e-13 and stats["pot_cycles"] >= 1
+    assert_parity(solver_fp64, 0, ref, 1e-11, fields=[I.PHI])
+
+
 @pytest.mark.slow
 def test_config_small_2000_steps(solver_fp64):
     """the 128 x 64 sessile-drop case (vertical field, Bo_m = 0.5, chi = 1, Ste = 0.1)"""
