@@ -479,100 +479,17 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
 
     // ---- phase 1: load the stage state with halo, ghost rules at walls ----------
     // All of a thread's region loads are issued before any is used (one memory latency
-    // per tile instead of one per region cell of the thread).  An interior tile, whose
-    // region lies inside the grid, has no ghost and no wrap: its region cell (lx, ly)
-    // is the grid cell (x0 - H + lx, y0 - H + ly).
-    const bool interior = x0 >= Gm::H && x0 + TX + Gm::H <= nx && y0 >= Gm::H && y0 + TY + Gm::H <= ny;
-    constexpr int ROUNDS = (RN + NT - 1) / NT;
-    HR lHe[ROUNDS];
-    R lC[ROUNDS], lP[ROUNDS], lMx[ROUNDS], lMy[ROUNDS], lPhi[ROUNDS];
-    size_t lGi[ROUNDS];
-    int lWall[ROUNDS];
-#pragma unroll
-    for (int i = 0; i < ROUNDS; ++i) {
-        const int k = threadIdx.x + i * NT;
-        if (k >= RN) break;
-        const int lx = k % RW, ly = k / RW;
-        const int gx = x0 - Gm::H + lx, gy = y0 - Gm::H + ly;
-        if (interior) {
-            const size_t gi = (size_t)gy * pitch + gx;
-            lGi[i] = gi;
-            lWall[i] = -1;
-            lHe[i] = gHe[gi];
-            lC[i] = gC[gi];
-            lP[i] = gP[gi];
-            lMx[i] = gMx[gi];
-            lMy[i] = gMy[gi];
-            lPhi[i] = gPhi[gi];
-            continue;
-        }
-        int sx, sy, xs, ys;  // source cell and status: 0 inside, 1 ghost low, 2 ghost high, 3 far
-        if (per_x) {
-            sx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
-            xs = 0;
-        } else if (gx >= 0 && gx < nx) {
-            sx = gx; xs = 0;
-        } else if (gx == -1) {
-            sx = 0; xs = 1;
-        } else if (gx == nx) {
-            sx = nx - 1; xs = 2;
-        } else {
-            sx = gx < 0 ? 0 : nx - 1; xs = 3;
-        }
-        if (per_y) {
-            sy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
-            ys = 0;
-        } else if (gy >= 0 && gy < ny) {
-            sy = gy; ys = 0;
-        } else if (gy == -1) {
-            sy = 0; ys = 1;
-        } else if (gy == ny) {
-            sy = ny - 1; ys = 2;
-        } else {
-            sy = gy < 0 ? 0 : ny - 1; ys = 3;
-        }
-        // a periodic halo can reach past one period only on grids narrower than the halo
-        sx = sx < 0 ? 0 : (sx >= nx ? nx - 1 : sx);
-        sy = sy < 0 ? 0 : (sy >= ny ? ny - 1 : sy);
-        int wall = -1;
-        signed char kd;
-        if (xs == 0 && ys == 0) {
-            kd = 0;
-        } else if ((xs == 1 || xs == 2) && ys == 0) {
-            wall = xs - 1;
-            kd = (signed char)(1 + wall);
-        } else if (xs == 0 && (ys == 1 || ys == 2)) {
-            wall = 2 + ys - 1;
-            kd = (signed char)(1 + wall);
-        } else {
-            kd = 5;
-        }
-        kind[k] = kd;
-        const size_t gi = (size_t)sy * pitch + sx;
-        lGi[i] = gi;
-        lWall[i] = wall;
-        lHe[i] = gHe[gi];
-        lC[i] = gC[gi];
-        lP[i] = gP[gi];
-        lMx[i] = gMx[gi];
-        lMy[i] = gMy[gi];
-        lPhi[i] = gPhi[gi];
-    }
-    __syncthreads();   // P and Q in shared memory
-#pragma unroll
-    for (int i = 0; i < ROUNDS; ++i) {
-        const int k = threadIdx.x + i * NT;
-        if (k >= RN) break;
-        const R C = lC[i];
+    // per tile instead of one per region cell of the thread).
+    // One region cell from its loaded stage state: T, F_l and the reconstruction H_e by
+    // Eq. 8, rho by Eq. 11, u = m / (rho / 3); at a wall ghost the mirror rules.
+    auto derive = [&](int k, HR He, R C, R pv, R mx, R my, R phi, int wall, size_t gi) {
         R T, Fl;
         R Hes;   // H_e for the reconstruction (enters only the interface T_f)
-        invert_state<R>(Q, lHe[i], C, T, Fl, &Hes);
+        invert_state<R>(Q, He, C, T, Fl, &Hes);
         const R Fs = R(1) - Fl;
         const R rho = mix(Fs, C, Q.rho_s, Q.rho_l, Q.rho_g);
         const R rinv = fdiv(R(3), rho);
-        R u = lMx[i] * rinv, v = lMy[i] * rinv;
-        R phi = lPhi[i];
-        const int wall = lWall[i];
+        R u = mx * rinv, v = my * rinv;
         if (wall >= 0) {
             u = -u;
             v = -v;
@@ -580,14 +497,14 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
             const R cp = mix(Fs, C, Q.cp_s, Q.cp_l, Q.cp_g);
             Hes = cp * T + Q.L * (R(1) - Fs);
             if (P.mag_dir[wall]) {
-                const int sx = (int)(lGi[i] % (size_t)pitch), sy = (int)(lGi[i] / (size_t)pitch);
+                const int sx = (int)(gi % (size_t)pitch), sy = (int)(gi / (size_t)pitch);
                 double wx = wall == 0 ? 0.0 : (wall == 1 ? (double)nx : sx + 0.5);
                 double wy = wall == 2 ? 0.0 : (wall == 3 ? (double)ny : sy + 0.5);
                 double pw = -P.H0 * (wx * P.cos_t + wy * P.sin_t);
                 phi = R(2.0 * pw) - phi;
             }
         }
-        s[SP * RN + k] = lP[i];
+        s[SP * RN + k] = pv;
         s[SU * RN + k] = u;
         s[SV * RN + k] = v;
         // a wall ghost's C follows the wetting rule (unchanged at 90 degrees, wet = 0)
@@ -597,6 +514,143 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         s[SFS * RN + k] = Fs;
         s[SRHO * RN + k] = rho;
         s[SPHI * RN + k] = phi;
+    };
+    // An interior tile, whose region lies inside the grid, has no ghost and no wrap: its
+    // region cell (lx, ly) is the grid cell (x0 - H + lx, y0 - H + ly).  The region's
+    // border ring, three cells from the tile, enters only the Laplacian of C and the
+    // gradient of phi in phase 2, so there an interior tile reads C and phi and derives
+    // nothing.
+    const bool interior = x0 >= Gm::H && x0 + TX + Gm::H <= nx && y0 >= Gm::H && y0 + TY + Gm::H <= ny;
+    if (interior) {
+        constexpr int IW = RW - 2, IN = IW * (RH - 2), IROUNDS = (IN + NT - 1) / NT;
+        constexpr int NB = 2 * (RW + RH) - 4;
+        static_assert(NB <= NT, "one border cell per thread");
+        const R* __restrict__ cbase = gC + (size_t)(y0 - Gm::H) * pitch + (x0 - Gm::H);
+        const R* __restrict__ pbase = gPhi + (size_t)(y0 - Gm::H) * pitch + (x0 - Gm::H);
+        const HR* __restrict__ hbase = gHe + (size_t)(y0 - Gm::H) * pitch + (x0 - Gm::H);
+        const R* __restrict__ qbase = gP + (size_t)(y0 - Gm::H) * pitch + (x0 - Gm::H);
+        const R* __restrict__ xbase = gMx + (size_t)(y0 - Gm::H) * pitch + (x0 - Gm::H);
+        const R* __restrict__ ybase = gMy + (size_t)(y0 - Gm::H) * pitch + (x0 - Gm::H);
+        HR lHe[IROUNDS];
+        R lC[IROUNDS], lP[IROUNDS], lMx[IROUNDS], lMy[IROUNDS], lPhi[IROUNDS];
+#pragma unroll
+        for (int i = 0; i < IROUNDS; ++i) {
+            const int t = threadIdx.x + i * NT;
+            if (t >= IN) break;
+            const int lx = 1 + t % IW, ly = 1 + t / IW;
+            const size_t o = (size_t)ly * pitch + lx;
+            lHe[i] = hbase[o];
+            lC[i] = cbase[o];
+            lP[i] = qbase[o];
+            lMx[i] = xbase[o];
+            lMy[i] = ybase[o];
+            lPhi[i] = pbase[o];
+        }
+        // the border ring: bottom row, top row, then the two side columns
+        int kb = -1;
+        R bC = 0, bPhi = 0;
+        if (threadIdx.x < NB) {
+            const int t = threadIdx.x;
+            int lx, ly;
+            if (t < RW) {
+                lx = t;
+                ly = 0;
+            } else if (t < 2 * RW) {
+                lx = t - RW;
+                ly = RH - 1;
+            } else {
+                const int u = t - 2 * RW;
+                lx = (u & 1) ? RW - 1 : 0;
+                ly = 1 + (u >> 1);
+            }
+            kb = ly * RW + lx;
+            const size_t o = (size_t)ly * pitch + lx;
+            bC = cbase[o];
+            bPhi = pbase[o];
+        }
+        __syncthreads();   // P and Q in shared memory
+        if (kb >= 0) {
+            s[SC * RN + kb] = bC;
+            s[SPHI * RN + kb] = bPhi;
+        }
+#pragma unroll
+        for (int i = 0; i < IROUNDS; ++i) {
+            const int t = threadIdx.x + i * NT;
+            if (t >= IN) break;
+            const int k = (1 + t / IW) * RW + 1 + t % IW;
+            derive(k, lHe[i], lC[i], lP[i], lMx[i], lMy[i], lPhi[i], -1, 0);
+        }
+    } else {
+        constexpr int ROUNDS = (RN + NT - 1) / NT;
+        HR lHe[ROUNDS];
+        R lC[ROUNDS], lP[ROUNDS], lMx[ROUNDS], lMy[ROUNDS], lPhi[ROUNDS];
+        size_t lGi[ROUNDS];
+        int lWall[ROUNDS];
+#pragma unroll
+        for (int i = 0; i < ROUNDS; ++i) {
+            const int k = threadIdx.x + i * NT;
+            if (k >= RN) break;
+            const int lx = k % RW, ly = k / RW;
+            const int gx = x0 - Gm::H + lx, gy = y0 - Gm::H + ly;
+            int sx, sy, xs, ys;  // source cell and status: 0 inside, 1 ghost low, 2 ghost high, 3 far
+            if (per_x) {
+                sx = gx < 0 ? gx + nx : (gx >= nx ? gx - nx : gx);
+                xs = 0;
+            } else if (gx >= 0 && gx < nx) {
+                sx = gx; xs = 0;
+            } else if (gx == -1) {
+                sx = 0; xs = 1;
+            } else if (gx == nx) {
+                sx = nx - 1; xs = 2;
+            } else {
+                sx = gx < 0 ? 0 : nx - 1; xs = 3;
+            }
+            if (per_y) {
+                sy = gy < 0 ? gy + ny : (gy >= ny ? gy - ny : gy);
+                ys = 0;
+            } else if (gy >= 0 && gy < ny) {
+                sy = gy; ys = 0;
+            } else if (gy == -1) {
+                sy = 0; ys = 1;
+            } else if (gy == ny) {
+                sy = ny - 1; ys = 2;
+            } else {
+                sy = gy < 0 ? 0 : ny - 1; ys = 3;
+            }
+            // a periodic halo can reach past one period only on grids narrower than the halo
+            sx = sx < 0 ? 0 : (sx >= nx ? nx - 1 : sx);
+            sy = sy < 0 ? 0 : (sy >= ny ? ny - 1 : sy);
+            int wall = -1;
+            signed char kd;
+            if (xs == 0 && ys == 0) {
+                kd = 0;
+            } else if ((xs == 1 || xs == 2) && ys == 0) {
+                wall = xs - 1;
+                kd = (signed char)(1 + wall);
+            } else if (xs == 0 && (ys == 1 || ys == 2)) {
+                wall = 2 + ys - 1;
+                kd = (signed char)(1 + wall);
+            } else {
+                kd = 5;
+            }
+            kind[k] = kd;
+            const size_t gi = (size_t)sy * pitch + sx;
+            lGi[i] = gi;
+            lWall[i] = wall;
+            lHe[i] = gHe[gi];
+            lC[i] = gC[gi];
+            lP[i] = gP[gi];
+            lMx[i] = gMx[gi];
+            lMy[i] = gMy[gi];
+            lPhi[i] = gPhi[gi];
+        }
+        __syncthreads();   // P and Q in shared memory
+#pragma unroll
+        for (int i = 0; i < ROUNDS; ++i) {
+            const int k = threadIdx.x + i * NT;
+            if (k >= RN) break;
+            derive(k, lHe[i], lC[i], lP[i], lMx[i], lMy[i], lPhi[i], lWall[i], lGi[i]);
+        }
     }
     __syncthreads();
     // ---- phase 2: mu_c and |H|^2 at inner cells; a wall ghost takes the values of
