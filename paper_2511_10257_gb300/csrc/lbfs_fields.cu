@@ -320,14 +320,19 @@ __global__ void k_step_finalize(const DevCase* __restrict__ cases, const int* __
         last = atomicAdd(&dc->tickets[0], 1u) == (unsigned)(kFinChunks - 1);
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last || threadIdx.x >= 32) return;
     __threadfence();
+    // the chunk sums, one per lane, combined by a fixed shuffle tree (the same order
+    // whichever block is last)
+    static_assert(kFinChunks <= 32, "one chunk per lane");
+    const int lane = threadIdx.x;
     double a[kRedN];
     for (int q = 0; q < kRedN; ++q) {
-        DSum<R> v = DSum<R>::zero();
-        for (int k = 0; k < kFinChunks; ++k) v.add(DSum<R>::of(ld_cg(&ch[k * kRedN + q])));
+        DSum<R> v = lane < kFinChunks ? DSum<R>::of(ld_cg(&ch[lane * kRedN + q])) : DSum<R>::zero();
+        for (int o = 16; o > 0; o >>= 1) v.shfl_add(o);
         a[q] = v.value();
     }
+    if (lane != 0) return;
     dc->tickets[0] = 0u;
     double* st = dc->stats;
     const double dt = dc->P.dt;

@@ -320,13 +320,19 @@ __global__ void k_mg_finalize(const DevCase* __restrict__ cases, const int* __re
         last = atomicAdd(&dc->tickets[1], 1u) == (unsigned)(kFinChunks - 1);
     }
     __syncthreads();
-    if (!last || threadIdx.x != 0) return;
+    if (!last || threadIdx.x >= 32) return;
     __threadfence();
-    DSum<M> R2 = DSum<M>::zero(), B2 = DSum<M>::zero();
-    for (int k = 0; k < kFinChunks; ++k) {
-        R2.add(DSum<M>::of(ld_cg(&ch[2 * k])));
-        B2.add(DSum<M>::of(ld_cg(&ch[2 * k + 1])));
+    // the chunk sums, one per lane, combined by a fixed shuffle tree (the same order
+    // whichever block is last)
+    static_assert(kFinChunks <= 32, "one chunk per lane");
+    const int lane = threadIdx.x;
+    DSum<M> R2 = lane < kFinChunks ? DSum<M>::of(ld_cg(&ch[2 * lane])) : DSum<M>::zero();
+    DSum<M> B2 = lane < kFinChunks ? DSum<M>::of(ld_cg(&ch[2 * lane + 1])) : DSum<M>::zero();
+    for (int o = 16; o > 0; o >>= 1) {
+        R2.shfl_add(o);
+        B2.shfl_add(o);
     }
+    if (lane != 0) return;
     dc->tickets[1] = 0u;
     const double rr = R2.value(), bb = B2.value();
     const double rel = bb > 0.0 ? sqrt(rr / bb) : sqrt(rr);
