@@ -45,6 +45,21 @@ def stage_bytes_per_cell(prec: int) -> float:
     return (s1 + s2 + s3) / 3.0
 
 
+# algorithmic bytes per cell of the potential solve of one step: the step's first
+# residual pass (read phi, mu_m; write r), then per refinement cycle the fine level's
+# down leg (read mu_m, r; write e; the restriction a quarter of that), its up leg (read
+# mu_m, r, e and a quarter cell of coarse correction; write e), the coarser levels (a
+# third of the fine level's legs), the correction (read phi and e, write phi) and the
+# residual pass again.  phi is 8 bytes (FP64, or an FP32 pair in mixed precision).
+def potential_bytes_per_cell(prec: int, cycles: float) -> float:
+    r = 8 if prec == 0 else 4
+    resid = 8 + r + r
+    down = 3 * r + (2 * r) / 4
+    up = 4 * r + r / 4
+    cycle = (down + up) * 4 / 3 + (8 + r + 8) + resid
+    return resid + cycles * cycle
+
+
 def workloads():
     from paper_2511_10257_gb300 import inputs as I
     return {
@@ -142,7 +157,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=self.out, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -150,7 +165,7 @@ class ClockSampler:
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        time.sleep(0.25)
+        time.sleep(0.06)   # the sample that falls due at the end of the timed region
         self.proc.terminate()
         self.proc.wait()
         self.out.flush()
@@ -446,6 +461,12 @@ def run_gpu(args):
                  "resid_max": max(x["pot_resid_max"] for x in timed_stats),
                  "cycles_mean": sum(x["pot_cycles_mean"] for x in timed_stats) / len(timed_stats),
                  "all_converged": all(x["pot_resid_max"] <= solver.mg_tol_used() for x in timed_stats)}
+    # the whole step against the same peak: three stage launches plus the potential's
+    # passes at the cycle count the timed steps ran
+    b_step = 3 * bpc + potential_bytes_per_cell(prec, potential["cycles_mean"])
+    roofline["step"] = {"bytes_per_cell": b_step, "achieved": value * 1e6 * b_step / 1e9,
+                        "frac": value * 1e6 * b_step / 1e9 / peak, "unit": "GB/s",
+                        "potential_bytes_per_cell": b_step - 3 * bpc}
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         import oracle
@@ -475,7 +496,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
-        "dtype": "f64" if prec == lbfs.FP64 else "f32+f64",
+        "dtype": "f64" if prec == lbfs.FP64 else "f32+f32x2",
         "data": "synthetic",
         "config": {"workload": name, "grid": grid, "cases": len(cases),
                    "precision": args.precision,

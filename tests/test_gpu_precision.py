@@ -4,7 +4,8 @@ The mixed path differs from FP64 in three ways: FP32 storage of p, the momenta a
 (H_e is an FP32 pair of about 48 bits), FP32 arithmetic in the fluxes and sources,
 and the potential solved to 1e-6 instead of 1e-13.  Each FP64 run below takes on one
 of these alone: the FP64 path with the mixed tolerance of the potential, and the FP64
-path with C, or with p and the momenta, rounded to FP32 after every step.  Their
+path with C, or with p and the momenta, rounded to FP32 after every step, or with H_e
+rounded to an FP32 pair (hi + lo) after every step.  Their
 freezing time (Eq. 51), liquid-fraction history Q_L and liquid-fraction field are
 compared with plain FP64 beside the mixed run's.  The printed table is the
 attribution; the assertions only check that each run froze and that the mixed run
@@ -20,18 +21,28 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 CHUNK = 500
 
 
-def _run(precision, max_steps=40000, mg_tol=0.0, round_ids=()):
+def _pair(x):
+    """x rounded to the nearest FP32 pair hi + lo (hi = fl32(x), lo = fl32(x - hi))"""
+    hi = x.astype(np.float32)
+    lo = (x - hi.astype(np.float64)).astype(np.float32)
+    return hi.astype(np.float64) + lo.astype(np.float64)
+
+
+def _run(precision, max_steps=40000, mg_tol=0.0, round_ids=(), pair_ids=()):
     c = I.config_small()
-    s = lbfs.Solver(precision=precision, max_cases=1, use_graph=not round_ids, mg_tol=mg_tol)
+    rounded = tuple(round_ids) + tuple(pair_ids)
+    s = lbfs.Solver(precision=precision, max_cases=1, use_graph=not rounded, mg_tol=mg_tol)
     s.set_case(0, c)
     fl, ql = [], []
     n, st = 0, None
     while n < max_steps:
-        if round_ids:
+        if rounded:
             for _ in range(CHUNK):
                 st = s.step(1)[0]
-                got = s.fields(0, list(round_ids))
-                s.set_fields(0, {f: got[f].astype(np.float32).astype(np.float64) for f in round_ids})
+                got = s.fields(0, list(rounded))
+                new = {f: got[f].astype(np.float32).astype(np.float64) for f in round_ids}
+                new.update({f: _pair(got[f]) for f in pair_ids})
+                s.set_fields(0, new)
         else:
             st = s.step(CHUNK)[0]
         n += CHUNK
@@ -50,6 +61,7 @@ def test_mixed_precision_error_attribution():
         "FP64, potential to 1e-6": _run(lbfs.FP64, mg_tol=1e-6),
         "FP64, C rounded to FP32": _run(lbfs.FP64, round_ids=(I.C,)),
         "FP64, p and momenta rounded to FP32": _run(lbfs.FP64, round_ids=(I.P, I.MX, I.MY)),
+        "FP64, H_e rounded to an FP32 pair": _run(lbfs.FP64, pair_ids=(I.HE,)),
     }
     print(f"\nFP64 freezing time {ref_t:.3f}")
     print("| run | freezing time rel. error | Q_L L-inf | F_l L-inf |")
