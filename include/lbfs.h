@@ -159,8 +159,9 @@ lbfs_status lbfs_create(const lbfs_config* cfg, lbfs_ctx** out);
 /* (Re)define case slot case_id (0 <= case_id < max_cases) and initialise its fields on
  * the host (Table 1 "Initialization": droplet C = 1/2 + 1/2 tanh(2 (R - r)/xi),
  * uniform T_init, liquid everywhere, p = 0, u = 0, phi the uniform far field), then
- * copy them to the device.  Checks the case (sizes, positive properties, dt against
- * the explicit diffusion limit) before any allocation; LBFS_EINVAL on failure. */
+ * copy them to the device.  Checks the case (sizes: nx, ny >= 4 and the padded row
+ * length, nx rounded up to 32, times ny below 2^31; positive properties; dt against the
+ * explicit diffusion limit) before any allocation; LBFS_EINVAL on failure. */
 lbfs_status lbfs_set_case(lbfs_ctx* ctx, int32_t case_id, const lbfs_case_desc* desc);
 
 /* Overwrite stored fields of a case from host FP64 arrays: the evolved state of Eq. 39

@@ -170,7 +170,9 @@ int stage_th(const lbfs_ctx* ctx) { return stage_tile_h(ctx->prec, ctx->tile); }
 lbfs_status resolve(lbfs_ctx* ctx, const lbfs_case_desc& d, CaseParams& P) {
     std::memset(&P, 0, sizeof(P));
     if (d.nx < 4 || d.ny < 4) return fail(ctx, LBFS_EINVAL, "nx and ny must be >= 4");
-    if ((int64_t)d.nx * d.ny > (int64_t)1 << 31) return fail(ctx, LBFS_EINVAL, "grid too large");
+    // cell indices (row pitch a multiple of 32 times ny) stay below 2^31 in 32-bit arithmetic
+    if ((int64_t)align_up((size_t)d.nx, 32) * d.ny >= (int64_t)1 << 31)
+        return fail(ctx, LBFS_EINVAL, "grid too large");
     if (d.flags != 0) return fail(ctx, LBFS_EINVAL, "flags must be 0");
     if (d.init < 0 || d.init > 2) return fail(ctx, LBFS_EINVAL, "init must be 0, 1 or 2");
     if (d.mag_bc < 0 || d.mag_bc > 1) return fail(ctx, LBFS_EINVAL, "mag_bc must be 0 or 1");

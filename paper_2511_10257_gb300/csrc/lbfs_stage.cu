@@ -458,7 +458,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         const int pc = threadIdx.x;
         const int gx = x0 + pc % TX, gy = y0 + pc / TX;
         if (gx < nx && gy < ny) {
-            const size_t gi = (size_t)gy * pitch + gx;
+            const unsigned gi = (unsigned)gy * (unsigned)pitch + (unsigned)gx;
             cp_async_elem(&pf_h[pc], gHe + gi);
             cp_async_elem(&pf_r[0 * TXY + pc], gP + gi);
             cp_async_elem(&pf_r[1 * TXY + pc], gMx + gi);
@@ -482,7 +482,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
     // per tile instead of one per region cell of the thread).
     // One region cell from its loaded stage state: T, F_l and the reconstruction H_e by
     // Eq. 8, rho by Eq. 11, u = m / (rho / 3); at a wall ghost the mirror rules.
-    auto derive = [&](int k, HR He, R C, R pv, R mx, R my, R phi, int wall, size_t gi) {
+    auto derive = [&](int k, HR He, R C, R pv, R mx, R my, R phi, int wall, unsigned gi) {
         R T, Fl;
         R Hes;   // H_e for the reconstruction (enters only the interface T_f)
         invert_state<R>(Q, He, C, T, Fl, &Hes);
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
             const R cp = mix(Fs, C, Q.cp_s, Q.cp_l, Q.cp_g);
             Hes = cp * T + Q.L * (R(1) - Fs);
             if (P.mag_dir[wall]) {
-                const int sx = (int)(gi % (size_t)pitch), sy = (int)(gi / (size_t)pitch);
+                const int sx = (int)(gi % (unsigned)pitch), sy = (int)(gi / (unsigned)pitch);
                 double wx = wall == 0 ? 0.0 : (wall == 1 ? (double)nx : sx + 0.5);
                 double wy = wall == 2 ? 0.0 : (wall == 3 ? (double)ny : sy + 0.5);
                 double pw = -P.H0 * (wx * P.cos_t + wy * P.sin_t);
@@ -538,7 +538,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
             const int t = threadIdx.x + i * NT;
             if (t >= IN) break;
             const int lx = 1 + t % IW, ly = 1 + t / IW;
-            const size_t o = (size_t)ly * pitch + lx;
+            const unsigned o = (unsigned)ly * (unsigned)pitch + (unsigned)lx;
             lHe[i] = hbase[o];
             lC[i] = cbase[o];
             lP[i] = qbase[o];
@@ -564,7 +564,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
                 ly = 1 + (u >> 1);
             }
             kb = ly * RW + lx;
-            const size_t o = (size_t)ly * pitch + lx;
+            const unsigned o = (unsigned)ly * (unsigned)pitch + (unsigned)lx;
             bC = cbase[o];
             bPhi = pbase[o];
         }
@@ -584,7 +584,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         constexpr int ROUNDS = (RN + NT - 1) / NT;
         HR lHe[ROUNDS];
         R lC[ROUNDS], lP[ROUNDS], lMx[ROUNDS], lMy[ROUNDS], lPhi[ROUNDS];
-        size_t lGi[ROUNDS];
+        unsigned lGi[ROUNDS];
         int lWall[ROUNDS];
 #pragma unroll
         for (int i = 0; i < ROUNDS; ++i) {
@@ -634,7 +634,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
                 kd = 5;
             }
             kind[k] = kd;
-            const size_t gi = (size_t)sy * pitch + sx;
+            const unsigned gi = (unsigned)sy * (unsigned)pitch + (unsigned)sx;
             lGi[i] = gi;
             lWall[i] = wall;
             lHe[i] = gHe[gi];
@@ -782,7 +782,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
         const R dhy = R(0.5) * (s[SH2 * RN + k + RW] - s[SH2 * RN + k - RW]);
         const R dmx = R(0.5) * (s[SMU * RN + k + 1] - s[SMU * RN + k - 1]);
         const R dmy = R(0.5) * (s[SMU * RN + k + RW] - s[SMU * RN + k - RW]);
-        const size_t gi = (size_t)gy * pitch + gx;
+        const unsigned gi = (unsigned)gy * (unsigned)pitch + (unsigned)gx;
         // lagged dF_s/dt: formed by stage 1 from F_s^n (this stage's own input) and the
         // previous step's F_s, which is then replaced by F_s^n
         R Sd;
@@ -827,7 +827,7 @@ __global__ void __launch_bounds__(NT, MINB) stage_kernel(const DevCase* __restri
             myn *= Fln;
             const R Fsn = R(1) - Fln;
             R* mu0 = static_cast<R*>(dc->lev[0].mu);
-            mu0[(size_t)gy * dc->lev[0].pitch + gx] = R(1) + mix(Fsn, Cn, Q.chi_s, Q.chi_l, Q.chi_g);
+            mu0[(unsigned)gy * (unsigned)dc->lev[0].pitch + (unsigned)gx] = R(1) + mix(Fsn, Cn, Q.chi_s, Q.chi_l, Q.chi_g);
             red_c[c] = Cn;
             red_h[c] = Hen;
             red_f[c] = Cn >= R(0.5) ? Fln : R(0);
