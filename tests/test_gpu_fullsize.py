@@ -1,5 +1,5 @@
 """Parity at the full workload sizes, in the launch configuration bench.py times
-(the autotuned 16 x 16 tile), on sampled outputs the oracle computes window by
+(the autotuned 32 x 8 tile), on sampled outputs the oracle computes window by
 window: one step of a cell depends only on cells within nine of it (three per
 Runge-Kutta stage) once the step's potential is fixed.  The GPU's state before a
 step, and the potential it solved for that step, are cut into windows; the oracle
@@ -22,7 +22,7 @@ pytestmark = [pytest.mark.gpu, pytest.mark.slow]
 STATE = [I.HE, I.P, I.C, I.MX, I.MY, I.FSPREV]
 CMP = [I.HE, I.P, I.C, I.MX, I.MY, I.T, I.FL]
 MARGIN = 12
-BENCH_TILE = 9   # the shape the autotuner keeps for these grids (16 x 16, four blocks of 256 threads per SM)
+BENCH_TILE = 10  # the shape the autotuner keeps for these grids (32 x 8, four blocks of 256 threads per SM)
 
 
 def _windows(nx, ny, R, angle):
