@@ -368,7 +368,8 @@ lbfs_status vcycle(lbfs_ctx* ctx) {
 }
 
 // The warm potential solve, recorded into the graph being captured on ctx->stream:
-// the step's first residual and check, then a conditional WHILE node whose body is one
+// in FP64 the linearly extrapolated start, then the step's first residual and check,
+// then a conditional WHILE node whose body is one
 // refinement cycle (V-cycle, correction, residual of the corrected potential, check).
 // The checks decide on the device whether the body runs again, so a step whose warm
 // start already meets mg_tol runs no cycle at all, and a step never runs more than
@@ -384,6 +385,10 @@ lbfs_status capture_warm_potential(lbfs_ctx* ctx) {
     if (cs != cudaStreamCaptureStatusActive || !g) return fail(ctx, LBFS_ECUDA, "potential capture is not active");
     cudaGraphConditionalHandle h;
     CK(cudaGraphConditionalHandleCreate(&h, g, 0, cudaGraphCondAssignDefault));
+    if (p == 0) {
+        LK(launch_mg_extrapolate(ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], ctx->d_pot, ctx->n_pot, s));
+        ++ctx->launches;
+    }
     LK(launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], 1, s));
     LK(launch_mg_finalize(p, ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, 1, K, nd, ticket, h, 1, s));
     const cudaGraphNode_t* deps = nullptr;
@@ -466,6 +471,11 @@ lbfs_status potential_solve(lbfs_ctx* ctx) {
         // the same cycles as plain launches; each kernel returns at once for a converged case
         const int K = ctx->mg_warm_cycles;
         int* nd = ctx->d_flag + 1;
+        if (p == 0) {
+            LK(launch_mg_extrapolate(ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], ctx->d_pot, ctx->n_pot,
+                                     s));
+            ++ctx->launches;
+        }
         LK(launch_mg_residual64(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], 1, s));
         LK(launch_mg_finalize(p, ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->mg_tol, 1, K, nd, nullptr, 0, 0, s));
         for (int c = 0; c < K; ++c) {
@@ -485,7 +495,7 @@ lbfs_status potential_solve(lbfs_ctx* ctx) {
             if (r != LBFS_OK) return r;
         }
         CK(cudaGraphLaunch(ctx->pot_exec, s));
-        ctx->launches += 2;
+        ctx->launches += p == 0 ? 4 : 2;   // (FP64: the extrapolated start) residual, check
         return LBFS_OK;
     }
     for (int it = 0;; ++it) {
@@ -504,6 +514,9 @@ lbfs_status potential_solve(lbfs_ctx* ctx) {
         if (r != LBFS_OK) return r;
         LK(launch_mg_correct(p, ctx->d_cases, ctx->d_mg_tiles[0], ctx->n_mg_tiles[0], s));
     }
+    // the warm steps that follow extrapolate only once they have stored a potential
+    for (size_t c = 0; c < ctx->slots.size(); ++c)
+        if (ctx->slots[c].defined) CK(cudaMemsetAsync(ctx->d_stats + c * kStatN + ST_EXTRAP, 0, sizeof(double), s));
     ctx->pot_fresh = false;
     return LBFS_OK;
 }
@@ -687,6 +700,7 @@ lbfs_status lbfs_set_case(lbfs_ctx* ctx, int32_t id, const lbfs_case_desc* desc)
     }
     if (ctx->prec == 0) {
         add((void**)&hd.phi64, cells * sizeof(double));
+        add((void**)&hd.phi_prev64, cells * sizeof(double));
     } else {
         add(&hd.phi, cells * rs);
         add((void**)&hd.phi_lo, cells * sizeof(float));

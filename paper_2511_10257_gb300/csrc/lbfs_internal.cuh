@@ -17,7 +17,7 @@ constexpr int kStatN = 20;      // per-case device statistics slots
 enum StatSlot {
     ST_SUM_C = 0, ST_SUM_HE, ST_SUM_FL_DROP, ST_N_DROP, ST_Q_L, ST_T, ST_T_FREEZE,
     ST_POT_RESID, ST_POT_CYCLES, ST_NONFINITE, ST_QL_PREV, ST_POT_DONE, ST_B2, ST_STEP,
-    ST_POT_FAIL, ST_POT_RESID_MAX, ST_POT_CYCLES_SUM, ST_STEPS_CALL, ST_SPARE0, ST_SPARE1
+    ST_POT_FAIL, ST_POT_RESID_MAX, ST_POT_CYCLES_SUM, ST_STEPS_CALL, ST_EXTRAP, ST_SPARE1
 };
 
 // Physical and numerical parameters of one case, resolved on the host in FP64.
@@ -72,6 +72,7 @@ struct DevCase {
     void* C[3];
     void* phi;        // potential read by the stage kernel (R); FP64 mode: the master
     double* phi64;    // FP64 mode: the master potential (== phi); mixed: unused
+    double* phi_prev64;  // FP64 mode: the previous step's potential; mixed: unused
     float* phi_lo;    // mixed: low word of the master potential phi + phi_lo (FP32 pair)
     void* Fs_prev;    // R: F_s of the previous step, replaced by F_s^n in stage 1
     void* Sdot;       // R: lagged dF_s/dt of the current step, written by stage 1

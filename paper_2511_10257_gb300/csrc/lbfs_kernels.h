@@ -36,6 +36,9 @@ cudaError_t launch_mg_finalize(int prec, const DevCase* cases, const int* case_i
                                int set_cond, cudaStream_t st);
 cudaError_t launch_mg_coarsest(int prec, const DevCase* cases, const int* case_ids, int ncases,
                                int max_cells, cudaStream_t st);
+// FP64 only: the linearly extrapolated warm start of the potential (two launches)
+cudaError_t launch_mg_extrapolate(const DevCase* cases, const TileRef* tiles, int n, const int* ids, int ncases,
+                                  cudaStream_t st);
 cudaError_t launch_mg_correct(int prec, const DevCase* cases, const TileRef* tiles, int n,
                               cudaStream_t st);
 size_t mg_coarsest_smem(int prec, int max_cells);

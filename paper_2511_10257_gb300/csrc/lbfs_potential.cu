@@ -824,6 +824,36 @@ __global__ void __launch_bounds__(kNT) k_correct(const DevCase* __restrict__ cas
     }
 }
 
+// The FP64 warm start, extrapolated linearly in time: phi <- 2 phi - phi_prev and
+// phi_prev <- phi, cell by cell, once phi_prev holds the previous step's potential
+// (ST_EXTRAP set); before that phi_prev <- phi only.  A start closer to the step's
+// potential needs fewer refinement cycles to reach the FP64 tolerance; the converged
+// potential is the same.  (The mixed path gains nothing from it: its potential moves
+// only on steps that run a cycle.)
+__global__ void __launch_bounds__(kNT) k_extrapolate(const DevCase* __restrict__ cases,
+                                                     const TileRef* __restrict__ tiles) {
+    const TileRef tr = tiles[blockIdx.x];
+    const DevCase* dc = cases + tr.case_id;
+    const MGLevel lv = dc->lev[0];
+    const int i = tr.x0 + threadIdx.x % kMgTX;
+    if (i >= lv.nx) return;
+    const bool valid = dc->stats[ST_EXTRAP] > 0.0;
+#pragma unroll
+    for (int q = 0; q < kRowsPT; ++q) {
+        const int j = tr.y0 + threadIdx.x / kMgTX + q * (kNT / kMgTX);
+        if (j >= lv.ny) break;
+        const size_t k = (size_t)j * lv.pitch + i;
+        const double v = dc->phi64[k];
+        if (valid) dc->phi64[k] = 2.0 * v - dc->phi_prev64[k];
+        dc->phi_prev64[k] = v;
+    }
+}
+
+// after k_extrapolate: phi_prev of every solving case now holds this step's start
+__global__ void k_extrapolate_commit(const DevCase* __restrict__ cases, const int* __restrict__ ids, int n) {
+    for (int c = threadIdx.x; c < n; c += blockDim.x) cases[ids[c]].stats[ST_EXTRAP] = 1.0;
+}
+
 // ---- the paper's own magnetic solver (Sec. 3.2, Eqs. 12-18) ----------------------
 // Explicit pseudo-time relaxation of Eq. 17, phi <- phi - dtau div F, with the LBFS
 // face flux of the magnetic distribution.  Per face (cell A below/left, B above/right,
@@ -1005,6 +1035,16 @@ cudaError_t launch_mg_coarsest(int prec, const DevCase* cases, const int* ids, i
             k_coarsest<float><<<ncases, 256, sm, st>>>(cases, ids);
         }
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mg_extrapolate(const DevCase* cases, const TileRef* tiles, int n, const int* ids, int ncases,
+                                  cudaStream_t st) {
+    if (n <= 0 || ncases <= 0) return cudaSuccess;
+    k_extrapolate<<<n, kNT, 0, st>>>(cases, tiles);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_extrapolate_commit<<<1, 128, 0, st>>>(cases, ids, ncases);
     return cudaGetLastError();
 }
 
