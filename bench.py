@@ -116,18 +116,23 @@ def stage_source_hash() -> str:
 
 def profiled(tile_name: str, grid: str, key: str):
     """a per-launch counter of the stage kernel from the committed ncu summary of this
-    kernel version, tile shape and grid (None when the kernel changed since the
-    capture): dram_bytes_per_launch_avg or warp_inst_per_launch"""
+    kernel version and grid, for the tile shape the autotuner kept (None when the
+    kernel changed since the capture or the shape was not captured):
+    dram_bytes_per_launch_avg or warp_inst_per_launch"""
     path = os.path.join(ROOT, "profiles", "stage_kernel_4096x2048.md")
     try:
-        kv = {}
+        common, tiles, cur = {}, {}, None
         for line in open(path):
             if line.startswith("- ") and ":" in line:
                 k, v = line[2:].split(":", 1)
-                kv[k.strip()] = v.strip().strip("`")
-        if (kv.get("source_sha256") == stage_source_hash() and kv.get("tile") == tile_name
-                and kv.get("grid") == grid):
-            return float(kv[key])
+                k, v = k.strip(), v.strip().strip("`")
+                if k == "tile":
+                    cur = tiles.setdefault(v, {})
+                else:
+                    (common if cur is None else cur)[k] = v
+        if (common.get("source_sha256") == stage_source_hash() and common.get("grid") == grid
+                and tile_name in tiles):
+            return float(tiles[tile_name][key])
     except Exception:
         return None
     return None
