@@ -56,7 +56,9 @@ def test_smallest_grid_matches_oracle():
 def test_arguments_are_checked():
     s = lbfs.Solver(precision=lbfs.MIXED, max_cases=2)
     bad_cases = [I.case(3, 16), I.case(16, 3), dict(I.case(16, 8), flags=1), I.case(16, 8, dt=2.0),
-                 I.case(65536, 65536, radius=10.0), I.case(16, 8, radius=0.0), I.case(16, 8, xi=0.0),
+                 I.case(65536, 65536, radius=10.0),
+                 I.case(33, 1 << 25, radius=10.0),   # 33 x 2^25 cells, but rows padded to 64: 2^31
+                 I.case(16, 8, radius=0.0), I.case(16, 8, xi=0.0),
                  I.case(16, 8, rho_l=0.0), I.case(16, 8, mu_l=-1.0)]
     for c in bad_cases:
         with pytest.raises(lbfs.LbfsError) as e:
