@@ -173,7 +173,9 @@ __device__ __forceinline__ float residual_cell_f(const DevCase* dc, const CasePa
     const float* mu = static_cast<const float*>(lv.mu);
     const float* hi = static_cast<const float*>(dc->phi);
     const float* lo = dc->phi_lo;
-    const size_t k = (size_t)j * lv.pitch + i;
+    // 32-bit cell indices: a level holds fewer than 2^31 cells (checked at set-up)
+    const unsigned pitch = (unsigned)lv.pitch;
+    const unsigned k = (unsigned)j * pitch + (unsigned)i;
     const float mc = mu[k], hc = hi[k], lc = lo[k];
     float ah = 0.f, al = 0.f;   // A phi as a pair
     double b = 0.0;
@@ -189,7 +191,7 @@ __device__ __forceinline__ float residual_cell_f(const DevCase* dc, const CasePa
     };
     if (i > 0 && i < lv.nx - 1 && j > 0 && j < lv.ny - 1) {
         // interior cell: four neighbour cells, no wall term (no FP64 instruction)
-        const size_t kw[4] = {k - 1, k + 1, k - lv.pitch, k + lv.pitch};
+        const unsigned kw[4] = {k - 1, k + 1, k - pitch, k + pitch};
 #pragma unroll
         for (int w = 0; w < 4; ++w) term(0.5f * (mc + mu[kw[w]]), hi[kw[w]], lo[kw[w]]);
         b_out = 0.0;
@@ -199,7 +201,7 @@ __device__ __forceinline__ float residual_cell_f(const DevCase* dc, const CasePa
         int ii, jj;
         float c, nh, nl;
         if (neighbour(P, lv.nx, lv.ny, i, j, w, ii, jj)) {
-            const size_t kn = (size_t)jj * lv.pitch + ii;
+            const unsigned kn = (unsigned)jj * pitch + (unsigned)ii;
             c = 0.5f * (mc + mu[kn]);
             nh = hi[kn];
             nl = lo[kn];
@@ -240,7 +242,7 @@ __global__ void __launch_bounds__(kNT) k_residual64(const DevCase* __restrict__ 
     for (int q = 0; q < kRowsPT; ++q) {
         const int j = tr.y0 + threadIdx.x / kMgTX + q * (kNT / kMgTX);
         if (i < lv.nx && j < lv.ny) {
-            const size_t k = (size_t)j * lv.pitch + i;
+            const unsigned k = (unsigned)j * (unsigned)lv.pitch + (unsigned)i;
             double b;
             if constexpr (sizeof(M) == 8) {
                 const double r = residual_cell<double>(dc, P, lv, i, j, b);
@@ -377,7 +379,7 @@ __device__ __forceinline__ M coarse_at(const CaseParams& P, const M* e, int nx, 
             if (P.mag_dir[w]) sgn = -sgn;
         }
     }
-    return sgn * e[(size_t)J * pitch + I];
+    return sgn * e[(unsigned)J * (unsigned)pitch + (unsigned)I];
 }
 
 // ---- fused V-cycle legs ------------------------------------------------------
@@ -508,7 +510,7 @@ __device__ __forceinline__ void region_load(const CaseParams& P, const MGLevel& 
     for (int k = threadIdx.x; k < G::N; k += blockDim.x) {
         int gx, gy, sx, sy;
         const int ok = region_source(P, lv.nx, lv.ny, x0, y0, H, G::W, k, gx, gy, sx, sy);
-        const size_t g = (size_t)sy * lv.pitch + sx;
+        const unsigned g = (unsigned)sy * (unsigned)lv.pitch + (unsigned)sx;
         in[k] = (unsigned char)ok;
         smu[k] = ok ? mu[g] : M(0);
         sr[k] = ok ? r[g] : M(0);
@@ -538,7 +540,7 @@ __global__ void __launch_bounds__(256) k_vdown(const DevCase* __restrict__ cases
     for (int t = threadIdx.x; t < kFTX * kFTY; t += blockDim.x) {
         const int gx = tr.x0 + t % kFTX, gy = tr.y0 + t / kFTX;
         if (gx < lv.nx && gy < lv.ny)
-            e[(size_t)gy * lv.pitch + gx] = se[(t / kFTX + kHD) * G::W + t % kFTX + kHD];
+            e[(unsigned)gy * (unsigned)lv.pitch + (unsigned)gx] = se[(t / kFTX + kHD) * G::W + t % kFTX + kHD];
     }
     // restricted residual r - A e over the children of each coarse cell (four, or
     // fewer where the coarse cell is the narrower last one of its row or column), and
@@ -553,14 +555,14 @@ __global__ void __launch_bounds__(256) k_vdown(const DevCase* __restrict__ cases
         {
             const int k0 = (kHD + 2 * cj) * G::W + kHD + 2 * ci;
             if (in[k0 + 1] && in[k0 + G::W]) {
-                muc[(size_t)J * cv.pitch + I] =
+                muc[(unsigned)J * (unsigned)cv.pitch + (unsigned)I] =
                     M(0.25) * ((smu[k0] + smu[k0 + 1]) + (smu[k0 + G::W] + smu[k0 + G::W + 1]));
             } else {
                 M m = smu[k0];
                 int n = 1;
                 if (in[k0 + 1]) { m += smu[k0 + 1]; ++n; }
                 if (in[k0 + G::W]) { m += smu[k0 + G::W]; ++n; }
-                muc[(size_t)J * cv.pitch + I] = m / M(n);
+                muc[(unsigned)J * (unsigned)cv.pitch + (unsigned)I] = m / M(n);
             }
         }
 #pragma unroll
@@ -570,7 +572,7 @@ __global__ void __launch_bounds__(256) k_vdown(const DevCase* __restrict__ cases
             if (!in[k]) continue;
             acc += sr[k] - region_apply<M, kHD>(P, lv, tr.x0, tr.y0, smu, se, in, k);
         }
-        rc[(size_t)J * cv.pitch + I] = acc;
+        rc[(unsigned)J * (unsigned)cv.pitch + (unsigned)I] = acc;
     }
 }
 
@@ -633,7 +635,7 @@ __global__ void __launch_bounds__(256) k_vup(const DevCase* __restrict__ cases,
     for (int t = threadIdx.x; t < kFTX * kFTY; t += blockDim.x) {
         const int gx = tr.x0 + t % kFTX, gy = tr.y0 + t / kFTX;
         if (gx < lv.nx && gy < lv.ny)
-            e[(size_t)gy * lv.pitch + gx] = se[(t / kFTX + kHU) * G::W + t % kFTX + kHU];
+            e[(unsigned)gy * (unsigned)lv.pitch + (unsigned)gx] = se[(t / kFTX + kHU) * G::W + t % kFTX + kHU];
     }
 }
 
@@ -809,7 +811,7 @@ __global__ void __launch_bounds__(kNT) k_correct(const DevCase* __restrict__ cas
     for (int q = 0; q < kRowsPT; ++q) {
         const int j = tr.y0 + threadIdx.x / kMgTX + q * (kNT / kMgTX);
         if (j >= lv.ny) break;
-        const size_t k = (size_t)j * lv.pitch + i;
+        const unsigned k = (unsigned)j * (unsigned)lv.pitch + (unsigned)i;
         if (sizeof(M) == 8) {
             const double v = dc->phi64[k] + (double)static_cast<const M*>(lv.e)[k];
             dc->phi64[k] = v;
@@ -842,7 +844,7 @@ __global__ void __launch_bounds__(kNT) k_extrapolate(const DevCase* __restrict__
     for (int q = 0; q < kRowsPT; ++q) {
         const int j = tr.y0 + threadIdx.x / kMgTX + q * (kNT / kMgTX);
         if (j >= lv.ny) break;
-        const size_t k = (size_t)j * lv.pitch + i;
+        const unsigned k = (unsigned)j * (unsigned)lv.pitch + (unsigned)i;
         const double v = dc->phi64[k];
         if (valid) dc->phi64[k] = 2.0 * v - dc->phi_prev64[k];
         dc->phi_prev64[k] = v;
