@@ -43,12 +43,14 @@ struct lbfs_ctx {
     std::vector<int> n_mg_tiles;
     std::vector<TileRef*> d_ft_tiles;   // fused V-cycle tiles per level
     std::vector<int> n_ft_tiles;
+    std::vector<int> ft_small;          // per level: 16 x 8 fused tiles instead of 32 x 16
     int* d_active = nullptr;
     int n_active = 0;
     int* d_pot = nullptr;
     int n_pot = 0;
     int max_depth = 0;
     int coarsest_cells = 0;
+    int sm_count = 152;               // multiprocessors of the context's device
     int* d_flag = nullptr;
     int* h_flag = nullptr;
     double* h_stats = nullptr;
@@ -296,7 +298,22 @@ lbfs_status rebuild(lbfs_ctx* ctx) {
         }
     }
     std::vector<std::vector<TileRef>> mg(depth), ft(depth);
-    for (int L = 0; L < depth; ++L)
+    // A level takes 16 x 8 fused tiles when its 32 x 16 tiles over all cases would
+    // leave most SMs idle (fewer than two a multiprocessor): the legs of a small grid
+    // then spread over four times as many SMs, at a larger halo share.
+    std::vector<int> small(depth, 0);
+    for (int L = 0; L < depth; ++L) {
+        long long big = 0;
+        for (int c : pot) {
+            const Slot& s = ctx->slots[c];
+            if (s.hd.nlev - 1 > L)
+                big += (long long)((s.hd.lev[L].nx + kFusedTX - 1) / kFusedTX) *
+                       ((s.hd.lev[L].ny + kFusedTY - 1) / kFusedTY);
+        }
+        small[L] = big > 0 && big < 2LL * ctx->sm_count ? 1 : 0;
+    }
+    for (int L = 0; L < depth; ++L) {
+        const int fx = small[L] ? kFusedSmallTX : kFusedTX, fy = small[L] ? kFusedSmallTY : kFusedTY;
         for (int c : pot) {
             const Slot& s = ctx->slots[c];
             if (s.hd.nlev <= L) continue;
@@ -305,10 +322,12 @@ lbfs_status rebuild(lbfs_ctx* ctx) {
                 for (int x = 0; x < s.hd.lev[L].nx; x += kMgTX) mg[L].push_back(TileRef{c, x, y, slot++});
             if (s.hd.nlev - 1 > L) {
                 slot = 0;
-                for (int y = 0; y < s.hd.lev[L].ny; y += kFusedTY)
-                    for (int x = 0; x < s.hd.lev[L].nx; x += kFusedTX) ft[L].push_back(TileRef{c, x, y, slot++});
+                for (int y = 0; y < s.hd.lev[L].ny; y += fy)
+                    for (int x = 0; x < s.hd.lev[L].nx; x += fx) ft[L].push_back(TileRef{c, x, y, slot++});
             }
         }
+    }
+    ctx->ft_small = small;
     auto upload = [&](void** dst, const void* src, size_t bytes) -> bool {
         if (*dst) dfree(ctx, *dst);
         *dst = nullptr;
@@ -360,10 +379,10 @@ lbfs_status vcycle(lbfs_ctx* ctx) {
     cudaStream_t s = ctx->stream;
     const int D = ctx->max_depth;
     for (int L = 0; L + 1 < D; ++L)
-        LK(launch_mg_vdown(p, ctx->d_cases, ctx->d_ft_tiles[L], ctx->n_ft_tiles[L], L, s));
+        LK(launch_mg_vdown(p, ctx->d_cases, ctx->d_ft_tiles[L], ctx->n_ft_tiles[L], L, ctx->ft_small[L], s));
     LK(launch_mg_coarsest(p, ctx->d_cases, ctx->d_pot, ctx->n_pot, ctx->coarsest_cells, s));
     for (int L = D - 2; L >= 0; --L)
-        LK(launch_mg_vup(p, ctx->d_cases, ctx->d_ft_tiles[L], ctx->n_ft_tiles[L], L, s));
+        LK(launch_mg_vup(p, ctx->d_cases, ctx->d_ft_tiles[L], ctx->n_ft_tiles[L], L, ctx->ft_small[L], s));
     return LBFS_OK;
 }
 
@@ -603,6 +622,12 @@ lbfs_status lbfs_create(const lbfs_config* cfg, lbfs_ctx** out) {
     ctx->mg_warm_cycles = cfg->mg_warm_cycles > 0 ? cfg->mg_warm_cycles : (ctx->prec == 0 ? 12 : 3);
     ctx->slots.resize(cfg->max_cases);
     ctx->tile = (cfg->tile >= 0 && cfg->tile < stage_tile_shapes()) ? cfg->tile : 0;
+    {
+        int n = 0;
+        if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, cfg->device) == cudaSuccess && n > 0)
+            ctx->sm_count = n;
+        cudaGetLastError();
+    }
     if (cfg->cuda_stream) {
         ctx->stream = static_cast<cudaStream_t>(cfg->cuda_stream);
     } else {

@@ -42,11 +42,13 @@ cudaError_t launch_mg_extrapolate(const DevCase* cases, const TileRef* tiles, in
 cudaError_t launch_mg_correct(int prec, const DevCase* cases, const TileRef* tiles, int n,
                               cudaStream_t st);
 size_t mg_coarsest_smem(int prec, int max_cells);
-// fused V-cycle legs over 32 x 16 tiles of one level (kFusedTX x kFusedTY)
+// fused V-cycle legs over 32 x 16 tiles of one level (kFusedTX x kFusedTY), or over
+// 16 x 8 tiles (small != 0) on a level whose 32 x 16 tiles would not fill the GPU
 constexpr int kFusedTX = 32, kFusedTY = 16;
-cudaError_t launch_mg_vdown(int prec, const DevCase* cases, const TileRef* tiles, int n, int level,
+constexpr int kFusedSmallTX = 16, kFusedSmallTY = 8;
+cudaError_t launch_mg_vdown(int prec, const DevCase* cases, const TileRef* tiles, int n, int level, int small,
                             cudaStream_t st);
-cudaError_t launch_mg_vup(int prec, const DevCase* cases, const TileRef* tiles, int n, int level,
+cudaError_t launch_mg_vup(int prec, const DevCase* cases, const TileRef* tiles, int n, int level, int small,
                           cudaStream_t st);
 
 // per-case utility kernels (lbfs_fields.cu)

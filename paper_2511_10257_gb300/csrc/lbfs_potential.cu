@@ -383,19 +383,18 @@ __device__ __forceinline__ M coarse_at(const CaseParams& P, const M* e, int nx, 
 }
 
 // ---- fused V-cycle legs ------------------------------------------------------
-// A block owns a kFTX x kFTY tile of one level and keeps it with a halo in shared
-// memory.  Red-black Gauss-Seidel half-sweeps shrink the valid region by one cell
+// A block owns a TX x TY tile of one level (32 x 16, or 16 x 8 on levels with too few
+// tiles to fill the GPU) and keeps it with a halo in shared memory.  Red-black Gauss-Seidel half-sweeps shrink the valid region by one cell
 // each, so after kFNu full sweeps the tile (plus one cell) holds exactly the values the
 // sweeps over the whole level would give.  Down leg: pre-smooth from e = 0, store e,
 // restrict r - A e to the next level.  Up leg: add the bilinear prolongation of the
 // coarse correction, post-smooth, store e.
-constexpr int kFTX = 32, kFTY = 16, kFNu = 2;
-static_assert(kFTX == kFusedTX && kFTY == kFusedTY, "the host's tile lists use the same tile");
+constexpr int kFNu = 2;
 constexpr int kHD = 2 * kFNu + 1, kHU = 2 * kFNu;
 
-template <int H>
+template <int TX, int TY, int H>
 struct FRegion {
-    static constexpr int W = kFTX + 2 * H, Hh = kFTY + 2 * H, N = W * Hh;
+    static constexpr int W = TX + 2 * H, Hh = TY + 2 * H, N = W * Hh;
 };
 
 // global position of region cell k of a tile at (x0, y0) with halo H; returns 0 if it
@@ -424,11 +423,11 @@ __device__ __forceinline__ int region_source(const CaseParams& P, int nx, int ny
 // (A x) at region cell k of a tile at (x0, y0), split into its diagonal and the
 // neighbour sum: A x = diag x_k - off.  Regular levels take the plain five-point
 // coefficients; a ragged level the geometric factors of its narrower last cells.
-template <class M, int H>
+template <class M, int TX, int TY, int H>
 __device__ __forceinline__ void region_stencil(const CaseParams& P, const MGLevel& lv, int x0, int y0,
                                                const M* mu, const M* x, const unsigned char* in, int k,
                                                M& diag, M& off) {
-    using G = FRegion<H>;
+    using G = FRegion<TX, TY, H>;
     const M mc = mu[k];
     diag = 0;
     off = 0;
@@ -461,10 +460,10 @@ __device__ __forceinline__ void region_stencil(const CaseParams& P, const MGLeve
 }
 
 // (A x) at region cell k in difference form, sum_f g mu_f (x_k - x_nb) + walls
-template <class M, int H>
+template <class M, int TX, int TY, int H>
 __device__ __forceinline__ M region_apply(const CaseParams& P, const MGLevel& lv, int x0, int y0, const M* mu,
                                           const M* x, const unsigned char* in, int k) {
-    using G = FRegion<H>;
+    using G = FRegion<TX, TY, H>;
     const M mc = mu[k], xc = x[k];
     M ax = 0;
     const int gx = x0 - H + k % G::W, gy = y0 - H + k / G::W;
@@ -481,11 +480,11 @@ __device__ __forceinline__ M region_apply(const CaseParams& P, const MGLevel& lv
     return ax;
 }
 
-template <class M, int H>
+template <class M, int TX, int TY, int H>
 __device__ __forceinline__ void region_half_sweep(const CaseParams& P, const MGLevel& lv, int x0, int y0,
                                                   const M* mu, const M* r, M* e, const unsigned char* in, int c,
                                                   int h) {
-    using G = FRegion<H>;
+    using G = FRegion<TX, TY, H>;
     const int VW = G::W - 2 * h, VH = G::Hh - 2 * h, HW = (VW + 1) / 2;
     const int base = (x0 - H) + (y0 - H);
     for (int t = threadIdx.x; t < HW * VH; t += blockDim.x) {
@@ -495,15 +494,15 @@ __device__ __forceinline__ void region_half_sweep(const CaseParams& P, const MGL
         const int k = ly * G::W + lx;
         if (!in[k]) continue;
         M diag, off;
-        region_stencil<M, H>(P, lv, x0, y0, mu, e, in, k, diag, off);
+        region_stencil<M, TX, TY, H>(P, lv, x0, y0, mu, e, in, k, diag, off);
         e[k] = fdiv(r[k] + off, diag);
     }
 }
 
-template <class M, int H>
+template <class M, int TX, int TY, int H>
 __device__ __forceinline__ void region_load(const CaseParams& P, const MGLevel& lv, int x0, int y0, M* smu,
                                             M* sr, M* se, unsigned char* in, bool load_e) {
-    using G = FRegion<H>;
+    using G = FRegion<TX, TY, H>;
     const M* mu = static_cast<const M*>(lv.mu);
     const M* r = static_cast<const M*>(lv.r);
     const M* e = static_cast<const M*>(lv.e);
@@ -518,10 +517,10 @@ __device__ __forceinline__ void region_load(const CaseParams& P, const MGLevel& 
     }
 }
 
-template <class M>
+template <class M, int TX, int TY>
 __global__ void __launch_bounds__(256) k_vdown(const DevCase* __restrict__ cases,
                                                const TileRef* __restrict__ tiles, int L) {
-    using G = FRegion<kHD>;
+    using G = FRegion<TX, TY, kHD>;
     __shared__ M smu[G::N], sr[G::N], se[G::N];
     __shared__ unsigned char in[G::N];
     const TileRef tr = tiles[blockIdx.x];
@@ -529,26 +528,26 @@ __global__ void __launch_bounds__(256) k_vdown(const DevCase* __restrict__ cases
     if (pot_done(dc) || L >= dc->nlev - 1) return;
     const CaseParams& P = dc->P;
     const MGLevel lv = dc->lev[L], cv = dc->lev[L + 1];
-    region_load<M, kHD>(P, lv, tr.x0, tr.y0, smu, sr, se, in, false);
+    region_load<M, TX, TY, kHD>(P, lv, tr.x0, tr.y0, smu, sr, se, in, false);
     __syncthreads();
     for (int h = 1; h <= 2 * kFNu; ++h) {
-        region_half_sweep<M, kHD>(P, lv, tr.x0, tr.y0, smu, sr, se, in, (h - 1) & 1, h);
+        region_half_sweep<M, TX, TY, kHD>(P, lv, tr.x0, tr.y0, smu, sr, se, in, (h - 1) & 1, h);
         __syncthreads();
     }
     // pre-smoothed correction of the tile
     M* e = static_cast<M*>(lv.e);
-    for (int t = threadIdx.x; t < kFTX * kFTY; t += blockDim.x) {
-        const int gx = tr.x0 + t % kFTX, gy = tr.y0 + t / kFTX;
+    for (int t = threadIdx.x; t < TX * TY; t += blockDim.x) {
+        const int gx = tr.x0 + t % TX, gy = tr.y0 + t / TX;
         if (gx < lv.nx && gy < lv.ny)
-            e[(unsigned)gy * (unsigned)lv.pitch + (unsigned)gx] = se[(t / kFTX + kHD) * G::W + t % kFTX + kHD];
+            e[(unsigned)gy * (unsigned)lv.pitch + (unsigned)gx] = se[(t / TX + kHD) * G::W + t % TX + kHD];
     }
     // restricted residual r - A e over the children of each coarse cell (four, or
     // fewer where the coarse cell is the narrower last one of its row or column), and
     // the coarse coefficient as the mean of the children's
     M* rc = static_cast<M*>(cv.r);
     M* muc = static_cast<M*>(cv.mu);
-    for (int t = threadIdx.x; t < (kFTX / 2) * (kFTY / 2); t += blockDim.x) {
-        const int ci = t % (kFTX / 2), cj = t / (kFTX / 2);
+    for (int t = threadIdx.x; t < (TX / 2) * (TY / 2); t += blockDim.x) {
+        const int ci = t % (TX / 2), cj = t / (TX / 2);
         const int I = tr.x0 / 2 + ci, J = tr.y0 / 2 + cj;
         if (I >= cv.nx || J >= cv.ny) continue;
         M acc = 0;
@@ -570,17 +569,17 @@ __global__ void __launch_bounds__(256) k_vdown(const DevCase* __restrict__ cases
             const int lx = kHD + 2 * ci + (q & 1), ly = kHD + 2 * cj + (q >> 1);
             const int k = ly * G::W + lx;
             if (!in[k]) continue;
-            acc += sr[k] - region_apply<M, kHD>(P, lv, tr.x0, tr.y0, smu, se, in, k);
+            acc += sr[k] - region_apply<M, TX, TY, kHD>(P, lv, tr.x0, tr.y0, smu, se, in, k);
         }
         rc[(unsigned)J * (unsigned)cv.pitch + (unsigned)I] = acc;
     }
 }
 
-template <class M>
+template <class M, int TX, int TY>
 __global__ void __launch_bounds__(256) k_vup(const DevCase* __restrict__ cases,
                                              const TileRef* __restrict__ tiles, int L) {
-    using G = FRegion<kHU>;
-    constexpr int CW = (kFTX + 2 * kHU) / 2 + 3, CH = (kFTY + 2 * kHU) / 2 + 3;
+    using G = FRegion<TX, TY, kHU>;
+    constexpr int CW = (TX + 2 * kHU) / 2 + 3, CH = (TY + 2 * kHU) / 2 + 3;
     __shared__ M smu[G::N], sr[G::N], se[G::N];
     __shared__ M sc[CW * CH];
     __shared__ unsigned char in[G::N];
@@ -589,7 +588,7 @@ __global__ void __launch_bounds__(256) k_vup(const DevCase* __restrict__ cases,
     if (pot_done(dc) || L >= dc->nlev - 1) return;
     const CaseParams& P = dc->P;
     const MGLevel lv = dc->lev[L], cv = dc->lev[L + 1];
-    region_load<M, kHU>(P, lv, tr.x0, tr.y0, smu, sr, se, in, true);
+    region_load<M, TX, TY, kHU>(P, lv, tr.x0, tr.y0, smu, sr, se, in, true);
     // coarse corrections around the region (one cell beyond its parents)
     const int cx0 = (tr.x0 - kHU) / 2 - 1 - ((tr.x0 - kHU) < 0 ? 1 : 0);
     const int cy0 = (tr.y0 - kHU) / 2 - 1 - ((tr.y0 - kHU) < 0 ? 1 : 0);
@@ -628,14 +627,14 @@ __global__ void __launch_bounds__(256) k_vup(const DevCase* __restrict__ cases,
     }
     __syncthreads();
     for (int h = 1; h <= 2 * kFNu; ++h) {
-        region_half_sweep<M, kHU>(P, lv, tr.x0, tr.y0, smu, sr, se, in, (h - 1) & 1, h);
+        region_half_sweep<M, TX, TY, kHU>(P, lv, tr.x0, tr.y0, smu, sr, se, in, (h - 1) & 1, h);
         __syncthreads();
     }
     M* e = static_cast<M*>(lv.e);
-    for (int t = threadIdx.x; t < kFTX * kFTY; t += blockDim.x) {
-        const int gx = tr.x0 + t % kFTX, gy = tr.y0 + t / kFTX;
+    for (int t = threadIdx.x; t < TX * TY; t += blockDim.x) {
+        const int gx = tr.x0 + t % TX, gy = tr.y0 + t / TX;
         if (gx < lv.nx && gy < lv.ny)
-            e[(unsigned)gy * (unsigned)lv.pitch + (unsigned)gx] = se[(t / kFTX + kHU) * G::W + t % kFTX + kHU];
+            e[(unsigned)gy * (unsigned)lv.pitch + (unsigned)gx] = se[(t / TX + kHU) * G::W + t % TX + kHU];
     }
 }
 
@@ -989,18 +988,29 @@ cudaError_t launch_mg_finalize(int prec, const DevCase* cases, const int* ids, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_mg_vdown(int prec, const DevCase* cases, const TileRef* tiles, int n, int L,
+cudaError_t launch_mg_vdown(int prec, const DevCase* cases, const TileRef* tiles, int n, int L, int small,
                             cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    if (prec == 0) k_vdown<double><<<n, 256, 0, st>>>(cases, tiles, L);
-    else k_vdown<float><<<n, 256, 0, st>>>(cases, tiles, L);
+    if (small) {
+        if (prec == 0) k_vdown<double, kFusedSmallTX, kFusedSmallTY><<<n, 128, 0, st>>>(cases, tiles, L);
+        else k_vdown<float, kFusedSmallTX, kFusedSmallTY><<<n, 128, 0, st>>>(cases, tiles, L);
+    } else {
+        if (prec == 0) k_vdown<double, kFusedTX, kFusedTY><<<n, 256, 0, st>>>(cases, tiles, L);
+        else k_vdown<float, kFusedTX, kFusedTY><<<n, 256, 0, st>>>(cases, tiles, L);
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_mg_vup(int prec, const DevCase* cases, const TileRef* tiles, int n, int L, cudaStream_t st) {
+cudaError_t launch_mg_vup(int prec, const DevCase* cases, const TileRef* tiles, int n, int L, int small,
+                          cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
-    if (prec == 0) k_vup<double><<<n, 256, 0, st>>>(cases, tiles, L);
-    else k_vup<float><<<n, 256, 0, st>>>(cases, tiles, L);
+    if (small) {
+        if (prec == 0) k_vup<double, kFusedSmallTX, kFusedSmallTY><<<n, 128, 0, st>>>(cases, tiles, L);
+        else k_vup<float, kFusedSmallTX, kFusedSmallTY><<<n, 128, 0, st>>>(cases, tiles, L);
+    } else {
+        if (prec == 0) k_vup<double, kFusedTX, kFusedTY><<<n, 256, 0, st>>>(cases, tiles, L);
+        else k_vup<float, kFusedTX, kFusedTY><<<n, 256, 0, st>>>(cases, tiles, L);
+    }
     return cudaGetLastError();
 }
 
